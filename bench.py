@@ -1,0 +1,320 @@
+"""Benchmark: FK-PK plain join at scale through the C-ABI (gj_join, PHJ-TR / GFTR).
+
+Workload: |R| = 2^25 unique int32 keys (a seeded permutation), |S| = 2^27 foreign
+keys drawn uniformly from R's keys (match ratio 1), 4 int32 payload columns per
+side, all materialised: T has 2^27 rows of 36 bytes. Metric: input tuples per
+second, (|R| + |S|) / time (the paper's join throughput, Sec. 5.1.2), in
+Gtuples/s. Inputs (3.4 GB) and output (4.8 GB) are far larger than the 129 MB L2,
+so no flush is needed between steps.
+
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+Under torchrun every rank runs an independent replica (the path has no exchange
+step on one GPU); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NR, NS, NCOLS = 1 << 25, 1 << 27, 4
+ROW_BYTES = 4 + 4 * NCOLS              # key + payloads of one input row
+OUT_ROW_BYTES = 4 + 4 * 2 * NCOLS      # T(key, r1..r4, s1..s4)
+MIN_BYTES = (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES
+WORKLOAD = (f"plain FK-PK join, |R|=2^25 unique int32 keys, |S|=2^27 uniform FK (theta=0), match ratio 1.0, "
+            f"{NCOLS} int32 payloads per side materialised (GFTR partitioned hash join)")
+SEED = 2023
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    for name in ("radix.cu", "join.cu", "gj_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2312_00720_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_digest") != kernel_source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock samples taken while the timed region runs."""
+
+    def __init__(self, device: int):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,utilization.gpu")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                rows.append(f)
+        load = [r for r in rows if r[7].replace(".", "").isdigit() and float(r[7]) > 50] or rows
+        sm = [float(r[0]) for r in load if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i in range(4) if r[3 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(load)}
+
+
+def cpu_baseline(sample_shift: int = 2):
+    """The oracle (single-threaded C++) on 1/2^sample_shift of the workload."""
+    import oracle
+    from paper_2312_00720_gb300 import workloads as wl
+
+    nr, ns = NR >> sample_shift, NS >> sample_shift
+    w = wl.join_workload(nr, ns, NCOLS, NCOLS, seed=SEED)
+    oracle.build()
+    t0 = time.perf_counter()
+    t = oracle.join(w["rkey"], w["rcols"], w["skey"], w["scols"])
+    dt = time.perf_counter() - t0
+    assert len(t) == ns
+    return {"value": (nr + ns) / dt / 1e9, "unit": "Gtuples/s", "cores": 1, "kind": "oracle",
+            "sample": f"|R|=2^{25 - sample_shift}, |S|=2^{27 - sample_shift} of the same workload "
+                      f"(same generator), single-threaded std::unordered_map join incl. materialisation, "
+                      f"{dt:.1f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("GJ_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2312_00720_gb300 import workloads as wl
+
+    shift = 3
+    nr, ns = NR >> shift, NS >> shift
+    w = wl.join_workload(nr, ns, NCOLS, NCOLS, seed=SEED)
+    oracle.build()
+    for _ in range(args.warmup if args.warmup <= 1 else 1):
+        oracle.join(w["rkey"][:1024], [c[:1024] for c in w["rcols"]], w["skey"][:4096],
+                    [c[:4096] for c in w["scols"]])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.join(w["rkey"], w["rcols"], w["skey"], w["scols"])
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = args.steps * (nr + ns) / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": "join input tuples/s ((|R|+|S|)/time)", "value": value,
+        "unit": "Gtuples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"each step joins |R|=2^{25 - shift}, |S|=2^{27 - shift}"},
+        "cpu_baseline": {"value": value, "unit": "Gtuples/s", "cores": 1, "kind": "oracle",
+                         "sample": f"|R|=2^{25 - shift}, |S|=2^{27 - shift} per step"},
+        "e2e": {"value": value, "unit": "Gtuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="phj_tr", choices=["phj_tr", "phj_ur", "nphj"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    from paper_2312_00720_gb300 import gj
+    from paper_2312_00720_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    gj.load()
+    w = wl.join_workload(NR, NS, NCOLS, NCOLS, seed=SEED)
+    dev = lambda a: torch.from_numpy(a).cuda()
+    rkey, skey = dev(w["rkey"]), dev(w["skey"])
+    rcols, scols = [dev(c) for c in w["rcols"]], [dev(c) for c in w["scols"]]
+    tkey = torch.empty(NS, dtype=torch.int32, device="cuda")
+    tcols = [torch.empty(NS, dtype=torch.int32, device="cuda") for _ in range(2 * NCOLS)]
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    step = lambda: gj.join(rkey, rcols, skey, scols, variant=args.variant, sync=False, out=(tkey, tcols), count=cnt)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.5)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert gj.device_status() == 0
+    assert int(cnt.item()) == NS, "join count differs from |S| x match ratio"
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = gj.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    launches = gj.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    assert gj.device_status() == 0
+    ms_step = ms / args.steps
+    value = world * (NR + NS) / (ms_step * 1e-3) / 1e9
+
+    # ---- per-kernel times on the launching stream (CUDA events around each launch)
+    gj.profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    prof = gj.profile_read()
+    gj.profile_enable(False)
+    alg_bytes_per_step = {
+        # two 8-bit passes over R and over S, each reading and writing key + payloads
+        "radix_scatter": 2 * 2 * (NR + NS) * ROW_BYTES,
+        # one read of every key for the histograms of both passes
+        "radix_hist": 4 * (NR + NS),
+        # read S' and R' once, write T
+        "phj_probe": (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES,
+        "partition_bounds": 4 * NR,
+    }
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    per_launch_bytes = alg_bytes_per_step.get(dom, 0) * args.steps / dom_launches
+    per_launch_s = dom_ms / dom_launches * 1e-3
+    peak, peak_src = load_peaks()
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    total_ms = sum(v[0] for v in prof.values())
+    kernel_split = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                        "share": v[0] / total_ms} for k, v in prof.items()}
+
+    # ---- end to end: pinned host inputs in, result rows out, every step
+    h_in = [torch.from_numpy(a).pin_memory() for a in [w["rkey"], *w["rcols"], w["skey"], *w["scols"]]]
+    d_in = [rkey, *rcols, skey, *scols]
+    h_out = [torch.empty(NS, dtype=torch.int32).pin_memory() for _ in range(1 + 2 * NCOLS)]
+    h_cnt = torch.empty(1, dtype=torch.int64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() * t.element_size() for t in h_out) + 8
+
+    def e2e_step():
+        for h, d in zip(h_in, d_in):
+            d.copy_(h, non_blocking=True)
+        step()
+        for h, d in zip(h_out, [tkey, *tcols]):
+            h.copy_(d, non_blocking=True)
+        h_cnt.copy_(cnt, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert int(h_cnt.item()) == NS
+    e2e_value = world * (NR + NS) / (e2e_ms * 1e-3) / 1e9
+
+    if rank == 0:
+        out = {
+            "metric": "join input tuples/s ((|R|+|S|)/time), plain FK-PK join at scale",
+            "value": value, "unit": "Gtuples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "variant": args.variant.upper().replace("_", "-"),
+                       "l2": "inputs 3.4 GB and output 4.8 GB exceed the 129 MB L2; no flush",
+                       "parallelism": f"{world} independent replica(s)", "seed": SEED},
+            "clocks": clk,
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "Gtuples/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic(dom),
+                         "alg_bytes_per_launch": per_launch_bytes},
+            # whole step against the minimal bytes (read R and S once, write T once)
+            "min_bytes_roofline": {
+                "bytes_per_step": MIN_BYTES,
+                "frac": MIN_BYTES / (ms_step * 1e-3) / 1e9 / peak},
+            "kernels": kernel_split,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * gj.h -- C ABI of the GB300 join / grouped-aggregation library (libgj.so).
+ *
+ * Operators (paper: "Efficiently Processing Joins and Grouped Aggregations on
+ * GPUs", PACMMOD 2025):
+ *   - inner equi-join T(key, r1.., s1..) of R(key, r1..) and S(key, s1..), R.key a
+ *     primary key and S.key a foreign key                       -- Sec. 2.2
+ *   - group-by R(k, r1..rn) -> A(k, a1..an) with reducible aggregates, the group
+ *     count g unknown in advance                                  -- Sec. 2.2, Alg. 1
+ *   - the radix-partition primitive: stable, partitions stored contiguously,
+ *     on bits [i, j) of the key                                   -- Sec. 2.3
+ *
+ * Conventions for every entry point
+ *   - Column data, outputs and counters are DEVICE pointers owned by the caller
+ *     and must stay valid until the work queued on `stream` has finished. The
+ *     descriptor structs themselves (gj_table, gj_options, arrays of ops) are
+ *     HOST memory and are read before the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is enqueued asynchronously; result counts are written to
+ *     device int64 words so that no call needs a host synchronisation.
+ *   - Scratch memory comes from the allocator set with gj_set_allocator, or from
+ *     cudaMallocAsync/cudaFreeAsync on `stream` when none is set. Scratch is
+ *     released (stream-ordered) before the call returns.
+ *   - Return value: argument errors are reported synchronously. Errors found by
+ *     the kernels (duplicate primary key, output capacity, a bounded wait that
+ *     ran out) are written to a device status word; with options.sync = 1 the
+ *     call synchronises `stream` and returns that status, otherwise read it with
+ *     gj_get_device_status. Kernels never trap.
+ *   - Row counts are limited to 2^30 - 1 per input (GJ_ERR_UNSUPPORTED above).
+ *   - Output row order is unspecified. PHJ-TR, PHJ-UR and SGB produce the same
+ *     order on every run (stable partitioning, no atomics deciding positions);
+ *     NPHJ, HGB and PGB assign positions through hash tables filled
+ *     concurrently, so their row order may differ between runs while the result
+ *     multiset does not.
+ */
+#ifndef GJ_H_
+#define GJ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GJ_MAX_COLS 8
+#define GJ_MAX_AGGS 32
+
+typedef enum {
+  GJ_OK = 0,
+  GJ_ERR_INVALID_ARG = 1,   /* bad pointer, type, count or option */
+  GJ_ERR_UNSUPPORTED = 2,   /* valid request outside what is implemented */
+  GJ_ERR_OOM = 3,           /* scratch allocation failed */
+  GJ_ERR_CAPACITY = 4,      /* result larger than the caller's capacity (rows past it are dropped) */
+  GJ_ERR_DUPLICATE_KEY = 5, /* R.key is not unique in gj_join (primary-key assumption, Sec. 2.2) */
+  GJ_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+  GJ_ERR_CUDA = 7           /* a CUDA runtime call failed */
+} gj_status;
+
+typedef enum { GJ_I32 = 0, GJ_I64 = 1 } gj_dtype;
+
+/* A columnar relation: one key column and up to GJ_MAX_COLS payload/value
+ * columns, each an array of n elements of its type (Sec. 3: relations are stored
+ * as columns, every column an array). */
+typedef struct {
+  int32_t key_type;               /* gj_dtype */
+  int32_t ncols;                  /* 0..GJ_MAX_COLS */
+  int64_t n;                      /* rows */
+  void* key;                      /* device, n elements */
+  int32_t col_type[GJ_MAX_COLS];  /* gj_dtype of each column */
+  void* cols[GJ_MAX_COLS];        /* device, n elements each */
+} gj_table;
+
+typedef enum { GJ_AGG_SUM = 0, GJ_AGG_COUNT = 1, GJ_AGG_MIN = 2, GJ_AGG_MAX = 3 } gj_agg;
+
+typedef enum {
+  GJ_JOIN_AUTO = 0,
+  GJ_JOIN_PHJ_TR = 1, /* radix-partitioned hash join, payloads partitioned with the keys (GFTR, Sec. 4.1.4) */
+  GJ_JOIN_PHJ_UR = 2, /* same partitioning of (key, tuple id), payloads gathered by id (GFUR, Sec. 3.1.2, 4.1.4) */
+  GJ_JOIN_NPHJ = 3    /* non-partitioned hash join: global table on R, S probed in order (Sec. 3.1.3) */
+} gj_join_variant;
+
+typedef enum {
+  GJ_GB_AUTO = 0,
+  GJ_GB_HGB = 1, /* hash-based, dense group ids then shared-memory aggregation (Sec. 4.2, Alg. 1) */
+  GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3) */
+  GJ_GB_PGB = 3  /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3) */
+} gj_groupby_variant;
+
+typedef enum { GJ_SELECT_HEURISTIC = 0, GJ_SELECT_MLP = 1 } gj_selector_mode;
+
+typedef struct {
+  int32_t join_variant;     /* gj_join_variant */
+  int32_t groupby_variant;  /* gj_groupby_variant */
+  int32_t selector;         /* gj_selector_mode used when a variant is AUTO */
+  int32_t radix_bits;       /* total partition bits for PHJ / PGB; 0 = choose from sizes */
+  int32_t bits_per_pass;    /* 1..8; 0 = balanced passes of at most 8 bits */
+  int32_t tile;             /* reserved for the tuner; 0 = default */
+  int32_t sync;             /* 1 = synchronise `stream` and return device-detected errors */
+  int32_t reserved;
+  float zipf_hint;          /* selector features (negative = unknown) */
+  float match_ratio_hint;
+  int64_t groups_hint;      /* expected group count, 0 = unknown */
+} gj_options;
+
+/* Fills *opt with the defaults (AUTO variants, heuristic selector, sync = 0). */
+void gj_options_default(gj_options* opt);
+
+/* Human-readable name of a status code; never NULL. */
+const char* gj_status_string(gj_status s);
+
+/* Scratch allocator hooks. alloc(bytes, stream, ctx) returns device memory or
+ * NULL (-> GJ_ERR_OOM); free(ptr, stream, ctx) releases it stream-ordered.
+ * Passing NULL for both restores cudaMallocAsync/cudaFreeAsync. Not thread-safe
+ * against concurrent calls of the other entry points. */
+gj_status gj_set_allocator(void* (*alloc)(size_t bytes, void* stream, void* ctx),
+                           void (*free_fn)(void* ptr, void* stream, void* ctx), void* ctx);
+
+/* Synchronises `stream`, returns the first error recorded by a kernel of this
+ * library on the current device since the last call, and clears it. */
+gj_status gj_get_device_status(void* stream);
+
+/* radix-partition (Sec. 2.3). Partitions the rows of `in` (key and every column)
+ * stably on bits [bit_lo, bit_hi) of d(key), where d is the key's own binary
+ * representation (key_transform 0), the key with its sign bit flipped so that
+ * digit order is signed order (1), or the MurmurHash3 fmix32/fmix64 finaliser of
+ * the key (2). bit_hi - bit_lo is 1..32 for 4-byte and 1..64 for 8-byte keys;
+ * digits of at most 8 bits are handled per pass, least significant first, so a
+ * full-width range is an LSD radix sort. `out` has the same types and ncols as
+ * `in`, with out->n >= in->n; its buffers must not overlap the input's.
+ * d_offsets (device, optional) receives 2^(bit_hi-bit_lo)+1 int64 partition
+ * bounds (partition p occupies rows [d_offsets[p], d_offsets[p+1])); it must be
+ * NULL when bit_hi - bit_lo > 24. */
+gj_status gj_radix_partition(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
+                             gj_table* out, int64_t* d_offsets, const gj_options* opt, void* stream);
+
+/* Inner equi-join (Sec. 2.2): T(key, R.cols.., S.cols..) = { (r.key, r.., s..) :
+ * r in R, s in S, r.key = s.key }. R.key must be unique (a primary key); a
+ * repeated key yields GJ_ERR_DUPLICATE_KEY. R and S keys have the same type.
+ * T has key_type = R.key_type, ncols = R.ncols + S.ncols with the R columns
+ * first, column types as in the inputs. Rows beyond T_capacity are dropped with
+ * GJ_ERR_CAPACITY; T_capacity >= S.n always suffices for a primary-key join.
+ * *d_T_count (device int64) receives |T|. */
+gj_status gj_join(const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,
+                  int64_t T_capacity, int64_t* d_T_count, void* stream);
+
+/* GROUP BY in.key with aggregate j = ops[j] over value column op_col[j]
+ * (COUNT ignores its column) -- Sec. 2.2, Alg. 1. Aggregates are int64; SUM
+ * wraps in two's complement. out_keys (device, in.key_type) and out_aggs[j]
+ * (device int64 each; the array of nagg pointers is host memory) receive one
+ * row per group; capacity >= number of groups (in.n always suffices), overflow
+ * -> GJ_ERR_CAPACITY. *d_ngroups (device int64) receives g. 1 <= nagg <= GJ_MAX_AGGS. */
+gj_status gj_groupby(const gj_table* in, int32_t nagg, const int32_t* ops, const int32_t* op_col,
+                     const gj_options* opt, void* out_keys, int64_t* const* out_aggs, int64_t capacity,
+                     int64_t* d_ngroups, void* stream);
+
+/* A column of the join result: side 0 = R, 1 = S; col = payload index on that
+ * side, or -1 for the join key. modulus > 0 applies C '%' (truncating) to the
+ * value, which is read as int64. */
+typedef struct {
+  int32_t side;
+  int32_t col;
+  int64_t modulus;
+} gj_colref;
+
+/* GROUP BY group_key over R join S with aggregate j = ops[j] over agg_cols[j]
+ * of the matching rows, without materialising the join result (the group-by
+ * that follows a join, Sec. 1). Group keys and aggregates are int64; out_keys
+ * (device int64) and out_aggs[j] (device int64) receive one row per group,
+ * capacity >= number of groups; *d_ngroups (device int64) receives g. R.key
+ * must be unique as in gj_join. */
+gj_status gj_join_groupby(const gj_table* R, const gj_table* S, gj_colref group_key, int32_t nagg,
+                          const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt,
+                          int64_t* out_keys, int64_t* const* out_aggs, int64_t capacity, int64_t* d_ngroups,
+                          void* stream);
+
+/* ---- Measurement support (no counterpart in the paper) -------------------
+ * gj_profile_enable(1) makes every kernel launch of the library record a CUDA
+ * event before and after itself on its stream; gj_profile_read synchronises the
+ * device, adds the elapsed times per kernel kind into ms[kind] and the launch
+ * counts into launches[kind] for kind < max_kinds (host arrays), clears the
+ * records and returns the number of kinds. gj_kernel_name(kind) names a kind.
+ * gj_kernel_launches() is the number of kernels launched by the library since
+ * load, counted whether or not timing is enabled. */
+void gj_profile_enable(int32_t on);
+int32_t gj_profile_read(double* ms, int64_t* launches, int32_t max_kinds);
+const char* gj_kernel_name(int32_t kind);
+int64_t gj_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H_ */

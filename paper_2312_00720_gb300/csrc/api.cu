@@ -1,0 +1,359 @@
+// C ABI entry points of libgj: argument validation, scratch allocation,
+// per-device status word, and dispatch to the operator pipelines.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "gj_internal.cuh"
+
+namespace gj {
+
+namespace {
+
+struct Allocator {
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free_fn)(void*, void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+Allocator g_alloc;
+
+constexpr int kMaxDevices = 64;
+int* g_status_word[kMaxDevices] = {nullptr};
+int g_num_sms[kMaxDevices] = {0};
+int g_smem_optin[kMaxDevices] = {0};
+bool g_pool_configured[kMaxDevices] = {false};
+std::mutex g_mu;
+
+bool valid_dtype(int t) { return t == GJ_I32 || t == GJ_I64; }
+
+gj_status check_table(const gj_table* t, bool need_key) {
+  if (!t) return GJ_ERR_INVALID_ARG;
+  if (!valid_dtype(t->key_type) || t->ncols < 0 || t->ncols > GJ_MAX_COLS || t->n < 0) return GJ_ERR_INVALID_ARG;
+  if (t->n > kMaxRows) return GJ_ERR_UNSUPPORTED;
+  if (t->n > 0 && need_key && !t->key) return GJ_ERR_INVALID_ARG;
+  for (int c = 0; c < t->ncols; ++c) {
+    if (!valid_dtype(t->col_type[c])) return GJ_ERR_INVALID_ARG;
+    if (t->n > 0 && !t->cols[c]) return GJ_ERR_INVALID_ARG;
+  }
+  return GJ_OK;
+}
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_timing{0};
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+std::vector<TimedLaunch> g_timed;
+std::vector<cudaEvent_t> g_event_pool;
+std::mutex g_prof_mu;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+const char* const kKindNames[KK_COUNT] = {
+    "radix_hist", "radix_scatter", "partition_bounds", "phj_probe", "nphj_build", "nphj_probe",
+    "hgb_group_id", "hgb_aggregate", "pgb", "sgb_reduce", "agg_init", "fused_probe", "group_emit",
+    "batch", "mlp"};
+
+}  // namespace
+
+LaunchScope::LaunchScope(const Ctx& ctx, int kind) : stream_(ctx.stream), kind_(kind) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (g_timing.load(std::memory_order_relaxed)) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    start_ = take_event();
+    cudaEventRecord(start_, stream_);
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (!start_) return;
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  cudaEvent_t end = take_event();
+  cudaEventRecord(end, stream_);
+  g_timed.push_back({kind_, start_, end});
+}
+
+gj_status cuda_check(cudaError_t e) { return e == cudaSuccess ? GJ_OK : GJ_ERR_CUDA; }
+
+Scratch::~Scratch() {
+  for (void* p : ptrs_) {
+    if (g_alloc.free_fn)
+      g_alloc.free_fn(p, (void*)stream_, g_alloc.ctx);
+    else
+      cudaFreeAsync(p, stream_);
+  }
+}
+
+void* Scratch::get(size_t bytes) {
+  if (failed_) return nullptr;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (g_alloc.alloc) {
+    p = g_alloc.alloc(bytes, (void*)stream_, g_alloc.ctx);
+  } else if (cudaMallocAsync(&p, bytes, stream_) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) {
+    failed_ = true;
+    return nullptr;
+  }
+  ptrs_.push_back(p);
+  return p;
+}
+
+gj_status make_ctx(void* stream, Ctx* ctx) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GJ_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_status_word[dev]) {
+    int* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return GJ_ERR_OOM;
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return GJ_ERR_CUDA;
+    g_status_word[dev] = p;
+    cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&g_smem_optin[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  if (!g_pool_configured[dev]) {
+    // keep freed scratch in the stream-ordered pool instead of returning it to
+    // the driver after every call
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    g_pool_configured[dev] = true;
+  }
+  ctx->stream = (cudaStream_t)stream;
+  ctx->d_status = g_status_word[dev];
+  ctx->num_sms = g_num_sms[dev];
+  ctx->smem_optin = g_smem_optin[dev];
+  ctx->device = dev;
+  return GJ_OK;
+}
+
+gj_status read_and_clear_status(const Ctx& ctx) {
+  int h = 0;
+  if (cudaStreamSynchronize(ctx.stream) != cudaSuccess) return GJ_ERR_CUDA;
+  if (cudaMemcpy(&h, ctx.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GJ_ERR_CUDA;
+  if (h != 0 && cudaMemset(ctx.d_status, 0, sizeof(int)) != cudaSuccess) return GJ_ERR_CUDA;
+  return (gj_status)h;
+}
+
+gj_status finish(const Ctx& ctx, const gj_options* opt, gj_status st) {
+  if (st != GJ_OK) return st;
+  if (opt && opt->sync) return read_and_clear_status(ctx);
+  return GJ_OK;
+}
+
+}  // namespace gj
+
+using namespace gj;
+
+extern "C" {
+
+void gj_options_default(gj_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->join_variant = GJ_JOIN_AUTO;
+  opt->groupby_variant = GJ_GB_AUTO;
+  opt->selector = GJ_SELECT_HEURISTIC;
+  opt->zipf_hint = -1.0f;
+  opt->match_ratio_hint = -1.0f;
+}
+
+const char* gj_status_string(gj_status s) {
+  switch (s) {
+    case GJ_OK: return "GJ_OK";
+    case GJ_ERR_INVALID_ARG: return "GJ_ERR_INVALID_ARG";
+    case GJ_ERR_UNSUPPORTED: return "GJ_ERR_UNSUPPORTED";
+    case GJ_ERR_OOM: return "GJ_ERR_OOM";
+    case GJ_ERR_CAPACITY: return "GJ_ERR_CAPACITY";
+    case GJ_ERR_DUPLICATE_KEY: return "GJ_ERR_DUPLICATE_KEY";
+    case GJ_ERR_TIMEOUT: return "GJ_ERR_TIMEOUT";
+    case GJ_ERR_CUDA: return "GJ_ERR_CUDA";
+  }
+  return "GJ_UNKNOWN_STATUS";
+}
+
+gj_status gj_set_allocator(void* (*alloc)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return GJ_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free_fn = free_fn;
+  g_alloc.ctx = ctx;
+  return GJ_OK;
+}
+
+gj_status gj_get_device_status(void* stream) {
+  Ctx ctx;
+  gj_status st = make_ctx(stream, &ctx);
+  if (st != GJ_OK) return st;
+  return read_and_clear_status(ctx);
+}
+
+gj_status gj_radix_partition(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
+                             gj_table* out, int64_t* d_offsets, const gj_options* opt, void* stream) {
+  gj_status st;
+  if ((st = check_table(in, true)) != GJ_OK) return st;
+  if ((st = check_table(out, true)) != GJ_OK) return st;
+  if (out->key_type != in->key_type || out->ncols != in->ncols || out->n < in->n) return GJ_ERR_INVALID_ARG;
+  for (int c = 0; c < in->ncols; ++c)
+    if (out->col_type[c] != in->col_type[c]) return GJ_ERR_INVALID_ARG;
+  const int kbits = in->key_type == GJ_I64 ? 64 : 32;
+  if (bit_lo < 0 || bit_hi <= bit_lo || bit_hi > kbits) return GJ_ERR_INVALID_ARG;
+  if (key_transform < 0 || key_transform > 2) return GJ_ERR_INVALID_ARG;
+  if (d_offsets && bit_hi - bit_lo > 24) return GJ_ERR_INVALID_ARG;
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (opt->bits_per_pass < 0 || opt->bits_per_pass > 8) return GJ_ERR_INVALID_ARG;
+  Ctx ctx;
+  if ((st = make_ctx(stream, &ctx)) != GJ_OK) return st;
+  ColSet cs{};
+  cs.n = in->ncols;
+  for (int c = 0; c < in->ncols; ++c) {
+    cs.src[c] = in->cols[c];
+    cs.dst[c] = out->cols[c];
+    cs.size[c] = dtype_size(in->col_type[c]);
+  }
+  {
+    Scratch scr(ctx.stream);
+    st = radix_partition_run(ctx, scr, in->key_type, in->key, out->key, cs, in->n, bit_lo, bit_hi, key_transform,
+                             opt->bits_per_pass);
+    if (st == GJ_OK && d_offsets)
+      st = partition_bounds_run(ctx, in->key_type, out->key, in->n, bit_lo, bit_hi - bit_lo, key_transform,
+                                d_offsets);
+  }
+  return finish(ctx, opt, st);
+}
+
+gj_status gj_join(const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T, int64_t T_capacity,
+                  int64_t* d_T_count, void* stream) {
+  gj_status st;
+  if ((st = check_table(R, true)) != GJ_OK) return st;
+  if ((st = check_table(S, true)) != GJ_OK) return st;
+  if (!T || !d_T_count || T_capacity < 0) return GJ_ERR_INVALID_ARG;
+  if (R->key_type != S->key_type || T->key_type != R->key_type) return GJ_ERR_INVALID_ARG;
+  if (T->ncols != R->ncols + S->ncols) return GJ_ERR_INVALID_ARG;
+  for (int c = 0; c < R->ncols; ++c)
+    if (T->col_type[c] != R->col_type[c]) return GJ_ERR_INVALID_ARG;
+  for (int c = 0; c < S->ncols; ++c)
+    if (T->col_type[R->ncols + c] != S->col_type[c]) return GJ_ERR_INVALID_ARG;
+  if (T_capacity > 0) {
+    if (!T->key) return GJ_ERR_INVALID_ARG;
+    for (int c = 0; c < T->ncols; ++c)
+      if (!T->cols[c]) return GJ_ERR_INVALID_ARG;
+  }
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (opt->join_variant < GJ_JOIN_AUTO || opt->join_variant > GJ_JOIN_NPHJ) return GJ_ERR_INVALID_ARG;
+  if (opt->radix_bits < 0 || opt->radix_bits > 16 || opt->bits_per_pass < 0 || opt->bits_per_pass > 8)
+    return GJ_ERR_INVALID_ARG;
+  Ctx ctx;
+  if ((st = make_ctx(stream, &ctx)) != GJ_OK) return st;
+  st = join_run(ctx, R, S, opt, T, T_capacity, d_T_count);
+  return finish(ctx, opt, st);
+}
+
+gj_status gj_groupby(const gj_table* in, int32_t nagg, const int32_t* ops, const int32_t* op_col,
+                     const gj_options* opt, void* out_keys, int64_t* const* out_aggs, int64_t capacity,
+                     int64_t* d_ngroups, void* stream) {
+  gj_status st;
+  if ((st = check_table(in, true)) != GJ_OK) return st;
+  if (nagg < 1 || nagg > GJ_MAX_AGGS || !ops || !op_col || !out_aggs || !d_ngroups || capacity < 0)
+    return GJ_ERR_INVALID_ARG;
+  for (int j = 0; j < nagg; ++j) {
+    if (ops[j] < GJ_AGG_SUM || ops[j] > GJ_AGG_MAX) return GJ_ERR_INVALID_ARG;
+    if (ops[j] != GJ_AGG_COUNT && (op_col[j] < 0 || op_col[j] >= in->ncols)) return GJ_ERR_INVALID_ARG;
+    if (capacity > 0 && !out_aggs[j]) return GJ_ERR_INVALID_ARG;
+  }
+  if (capacity > 0 && !out_keys) return GJ_ERR_INVALID_ARG;
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (opt->groupby_variant < GJ_GB_AUTO || opt->groupby_variant > GJ_GB_PGB) return GJ_ERR_INVALID_ARG;
+  if (opt->radix_bits < 0 || opt->radix_bits > 24 || opt->bits_per_pass < 0 || opt->bits_per_pass > 8)
+    return GJ_ERR_INVALID_ARG;
+  Ctx ctx;
+  if ((st = make_ctx(stream, &ctx)) != GJ_OK) return st;
+  st = groupby_run(ctx, in, nagg, ops, op_col, opt, out_keys, out_aggs, capacity, d_ngroups);
+  return finish(ctx, opt, st);
+}
+
+gj_status gj_join_groupby(const gj_table* R, const gj_table* S, gj_colref group_key, int32_t nagg,
+                          const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt, int64_t* out_keys,
+                          int64_t* const* out_aggs, int64_t capacity, int64_t* d_ngroups, void* stream) {
+  gj_status st;
+  if ((st = check_table(R, true)) != GJ_OK) return st;
+  if ((st = check_table(S, true)) != GJ_OK) return st;
+  if (R->key_type != S->key_type) return GJ_ERR_INVALID_ARG;
+  auto ref_ok = [&](const gj_colref& r) {
+    if (r.side != 0 && r.side != 1) return false;
+    const gj_table* t = r.side == 0 ? R : S;
+    return r.col >= -1 && r.col < t->ncols && r.modulus >= 0;
+  };
+  if (!ref_ok(group_key)) return GJ_ERR_INVALID_ARG;
+  if (nagg < 1 || nagg > GJ_MAX_AGGS || !ops || !agg_cols || !out_aggs || !d_ngroups || capacity < 0)
+    return GJ_ERR_INVALID_ARG;
+  for (int j = 0; j < nagg; ++j) {
+    if (ops[j] < GJ_AGG_SUM || ops[j] > GJ_AGG_MAX) return GJ_ERR_INVALID_ARG;
+    if (ops[j] != GJ_AGG_COUNT && !ref_ok(agg_cols[j])) return GJ_ERR_INVALID_ARG;
+    if (capacity > 0 && !out_aggs[j]) return GJ_ERR_INVALID_ARG;
+  }
+  if (capacity > 0 && !out_keys) return GJ_ERR_INVALID_ARG;
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (opt->join_variant < GJ_JOIN_AUTO || opt->join_variant > GJ_JOIN_NPHJ) return GJ_ERR_INVALID_ARG;
+  if (opt->radix_bits < 0 || opt->radix_bits > 16 || opt->bits_per_pass < 0 || opt->bits_per_pass > 8)
+    return GJ_ERR_INVALID_ARG;
+  Ctx ctx;
+  if ((st = make_ctx(stream, &ctx)) != GJ_OK) return st;
+  st = join_groupby_run(ctx, R, S, group_key, nagg, ops, agg_cols, opt, out_keys, out_aggs, capacity, d_ngroups);
+  return finish(ctx, opt, st);
+}
+
+void gj_profile_enable(int32_t on) { g_timing.store(on ? 1 : 0); }
+
+int32_t gj_profile_read(double* ms, int64_t* launches, int32_t max_kinds) {
+  cudaDeviceSynchronize();
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  for (int k = 0; k < max_kinds && k < KK_COUNT; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+  }
+  for (auto& t : g_timed) {
+    float e = 0.f;
+    cudaEventElapsedTime(&e, t.a, t.b);
+    if (t.kind < max_kinds) {
+      if (ms) ms[t.kind] += e;
+      if (launches) launches[t.kind] += 1;
+    }
+    g_event_pool.push_back(t.a);
+    g_event_pool.push_back(t.b);
+  }
+  g_timed.clear();
+  return KK_COUNT;
+}
+
+const char* gj_kernel_name(int32_t kind) { return kind >= 0 && kind < KK_COUNT ? kKindNames[kind] : "unknown"; }
+
+int64_t gj_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

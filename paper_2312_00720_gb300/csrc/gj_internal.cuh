@@ -1,0 +1,239 @@
+// Internal declarations shared by the CUDA translation units of libgj.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gj.h"
+
+namespace gj {
+
+constexpr int kMaxCols = GJ_MAX_COLS;
+constexpr int kMaxAggs = GJ_MAX_AGGS;
+constexpr int64_t kMaxRows = (int64_t(1) << 30) - 1;
+
+// Bounded spin for cross-block waits: after this many polls the waiter records
+// GJ_ERR_TIMEOUT and proceeds with what it has, so a kernel always terminates.
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+// ------------------------------------------------------------------ hashing
+// MurmurHash3 fmix32 / fmix64 finalisers (Appleby, public domain): bijective
+// mixes; partition digits take the low bits, hash-table slots the bits above.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+enum KeyTransform { kRawBits = 0, kSignedOrder = 1, kHashed = 2 };
+
+template <typename K>
+struct KeyTraits;
+template <>
+struct KeyTraits<int32_t> {
+  using U = uint32_t;
+  static constexpr int kBits = 32;
+  __host__ __device__ static uint32_t hash(int32_t k) { return fmix32((uint32_t)k); }
+  __host__ __device__ static uint64_t hash64(int32_t k) { return fmix32((uint32_t)k); }
+};
+template <>
+struct KeyTraits<int64_t> {
+  using U = uint64_t;
+  static constexpr int kBits = 64;
+  __host__ __device__ static uint64_t hash(int64_t k) { return fmix64((uint64_t)k); }
+  __host__ __device__ static uint64_t hash64(int64_t k) { return fmix64((uint64_t)k); }
+};
+
+// The bit pattern whose bits [lo, hi) form a key's radix digit.
+template <typename K>
+__host__ __device__ __forceinline__ typename KeyTraits<K>::U digit_source(K k, int transform) {
+  using U = typename KeyTraits<K>::U;
+  U u = (U)k;
+  if (transform == kSignedOrder) u ^= (U(1) << (KeyTraits<K>::kBits - 1));
+  if (transform == kHashed) u = (U)KeyTraits<K>::hash(k);
+  return u;
+}
+
+template <typename K>
+__host__ __device__ __forceinline__ uint32_t extract_digit(K k, int transform, int shift, int width) {
+  auto u = digit_source<K>(k, transform);
+  return (uint32_t)((u >> shift) & ((typename KeyTraits<K>::U(1) << width) - 1));
+}
+
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------------ status
+__device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
+
+// ------------------------------------------------------------------ look-back
+// Chained scan across tiles taken in order (decoupled look-back, Merrill &
+// Garland 2016). A tile's 64-bit word holds a 2-bit flag in the top bits and a
+// 62-bit count: 1 = aggregate of this tile only, 2 = inclusive prefix.
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagInc = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) { return *(volatile const uint64_t*)p; }
+__device__ __forceinline__ void st_volatile(uint64_t* p, uint64_t v) { *(volatile uint64_t*)p = v; }
+__device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+__device__ __forceinline__ void st_volatile32(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
+
+// Called by one thread of tile `tile`: publishes `agg`, returns the exclusive
+// prefix over tiles 0..tile-1 and publishes the inclusive value.
+__device__ __forceinline__ uint64_t lookback_scan(uint64_t* st, int64_t tile, uint64_t agg, int* status) {
+  if (tile == 0) {
+    st_volatile(&st[0], kFlagInc | agg);
+    return 0;
+  }
+  st_volatile(&st[tile], kFlagAgg | agg);
+  uint64_t excl = 0;
+  int64_t t = tile - 1;
+  uint32_t spins = 0;
+  while (t >= 0) {
+    uint64_t w = ld_volatile(&st[t]);
+    if ((w & ~kValMask) == 0) {
+      if (++spins > kSpinLimit) {
+        set_status(status, GJ_ERR_TIMEOUT);
+        break;
+      }
+      continue;
+    }
+    excl += w & kValMask;
+    if ((w & ~kValMask) == kFlagInc) break;
+    --t;
+  }
+  st_volatile(&st[tile], kFlagInc | (excl + agg));
+  return excl;
+}
+
+// ------------------------------------------------------------------ columns
+struct ColSet {
+  const void* src[kMaxCols];
+  void* dst[kMaxCols];
+  int32_t size[kMaxCols];  // bytes per element: 4 or 8
+  int32_t n;
+};
+
+__host__ __device__ __forceinline__ int dtype_size(int t) { return t == GJ_I64 ? 8 : 4; }
+
+__device__ __forceinline__ int64_t load_as_i64(const void* p, int size, int64_t i) {
+  return size == 8 ? ((const int64_t*)p)[i] : (int64_t)((const int32_t*)p)[i];
+}
+
+__device__ __forceinline__ void copy_elem(void* dst, int64_t o, const void* src, int64_t i, int size) {
+  if (size == 8)
+    ((int64_t*)dst)[o] = ((const int64_t*)src)[i];
+  else
+    ((int32_t*)dst)[o] = ((const int32_t*)src)[i];
+}
+
+// ------------------------------------------------------------------ host side
+struct Ctx {
+  cudaStream_t stream;
+  int* d_status;  // per-device persistent status word
+  int num_sms;
+  int smem_optin;
+  int device;
+};
+
+// Stream-ordered scratch allocations released when the object goes away.
+class Scratch {
+ public:
+  explicit Scratch(cudaStream_t s) : stream_(s) {}
+  ~Scratch();
+  void* get(size_t bytes);  // NULL on failure (sticky failed() flag)
+  template <typename T>
+  T* get_as(size_t count) {
+    return (T*)get(count * sizeof(T));
+  }
+  bool failed() const { return failed_; }
+
+ private:
+  cudaStream_t stream_;
+  std::vector<void*> ptrs_;
+  bool failed_ = false;
+};
+
+gj_status make_ctx(void* stream, Ctx* ctx);
+
+// Kernel kinds for launch counting and the optional per-kernel event timing.
+enum KernelKind {
+  KK_RADIX_HIST = 0,
+  KK_RADIX_SCATTER,
+  KK_PART_BOUNDS,
+  KK_PHJ_PROBE,
+  KK_NPHJ_BUILD,
+  KK_NPHJ_PROBE,
+  KK_HGB_GROUP_ID,
+  KK_HGB_AGG,
+  KK_PGB,
+  KK_SGB_REDUCE,
+  KK_AGG_INIT,
+  KK_FUSED_PROBE,
+  KK_GROUP_EMIT,
+  KK_BATCH,
+  KK_MLP,
+  KK_COUNT
+};
+// Brackets one kernel launch: counts it and, when timing is on, records CUDA
+// events before and after it on the launching stream.
+class LaunchScope {
+ public:
+  LaunchScope(const Ctx& ctx, int kind);
+  ~LaunchScope();
+
+ private:
+  cudaStream_t stream_;
+  int kind_;
+  cudaEvent_t start_ = nullptr;
+};
+gj_status finish(const Ctx& ctx, const gj_options* opt, gj_status st);
+gj_status cuda_check(cudaError_t e);
+
+// ------------------------------------------------------------------ radix partition
+// Per-pass plan for a stable partition on bits [lo, hi): LSD passes of <= 8 bits.
+struct RadixPlan {
+  int passes;
+  int shift[16];
+  int width[16];
+};
+RadixPlan make_radix_plan(int lo, int hi, int bits_per_pass);
+
+// Partitions key + columns (cols.src -> cols.dst; src NULL with gen_tid set means
+// "row index as int32") from kin to kout. Scratch ping-pong buffers come from `scr`.
+gj_status radix_partition_run(const Ctx& ctx, Scratch& scr, int key_type, const void* kin, void* kout,
+                              const ColSet& cols, int64_t n, int lo, int hi, int transform, int bits_per_pass);
+
+// Partition bounds of already-partitioned keys: off[p] = first row with digit >= p.
+gj_status partition_bounds_run(const Ctx& ctx, int key_type, const void* keys, int64_t n, int lo, int width,
+                               int transform, int64_t* d_off);
+
+// ------------------------------------------------------------------ operators
+gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,
+                   int64_t cap, int64_t* d_count);
+gj_status groupby_run(const Ctx& ctx, const gj_table* in, int nagg, const int32_t* ops, const int32_t* op_col,
+                      const gj_options* opt, void* out_keys, int64_t* const* out_aggs, int64_t cap,
+                      int64_t* d_ngroups);
+gj_status join_groupby_run(const Ctx& ctx, const gj_table* R, const gj_table* S, gj_colref gk, int nagg,
+                           const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt, int64_t* out_keys,
+                           int64_t* const* out_aggs, int64_t cap, int64_t* d_ngroups);
+
+// Total partition bits for a build side of nr rows so that a partition holds
+// about `target` rows; at most 16 bits (two passes of 8).
+int choose_join_bits(int64_t nr, int64_t target);
+
+}  // namespace gj

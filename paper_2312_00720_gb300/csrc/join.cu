@@ -1,0 +1,421 @@
+// Joins (paper Sec. 3.1 and 4.1.4).
+//
+// PHJ-TR / PHJ-UR: both relations are radix-partitioned on hashed key bits with
+// the stable radix-partition primitive (contiguous partitions, bounds from a
+// histogram-like pass), then matches are found with a shared-memory hash table
+// per build-side partition, and the result is materialised.
+//   * TR (GFTR, Sec. 4.1.2 / 4.1.4): payload columns are partitioned together
+//     with the key, so S payloads are read sequentially and R payloads from the
+//     small, contiguous partition R'_p (clustered).
+//   * UR (GFUR, Fig. gfur): (key, tuple id) pairs are partitioned and payloads
+//     are gathered from the untransformed inputs through the ids.
+// The probe side is walked in fixed-size tiles of the partitioned S'. A tile
+// covers the tail of one partition, whole partitions or a slice of a large
+// one; each partition slice rebuilds the table of R'_p, which is the paper's
+// decomposition of large probe partitions (Sec. 3.1.2 / 4.1.4) done by
+// construction, so skewed foreign keys do not unbalance the blocks. Output
+// positions come from a decoupled look-back over tiles, so the result is
+// compact, ordered by S' and identical on every run.
+//
+// NPHJ (Sec. 3.1.3): one global open-addressing table on R (key -> row), S
+// probed in its own order; R payloads are gathered randomly, S sequentially.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gj_internal.cuh"
+
+namespace gj {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTileS = 2048;          // probe rows per tile
+constexpr int kItems = kTileS / kThreads;
+constexpr int kBuildCap = 2048;       // build rows per shared-memory table
+constexpr int kSlots = 2 * kBuildCap; // load factor <= 1/2
+
+struct JoinIO {
+  // R side: value of R column c for match m = rsrc[c][ r_tid ? r_tid[m] : m ]
+  const void* rsrc[kMaxCols];
+  int32_t rsize[kMaxCols];
+  int32_t nr_cols;
+  const int32_t* r_tid;  // UR: tuple ids carried through the partitioning of R
+  // S side: value of S column c for probe row i = ssrc[c][ s_tid ? s_tid[i] : i ]
+  const void* ssrc[kMaxCols];
+  int32_t ssize[kMaxCols];
+  int32_t ns_cols;
+  const int32_t* s_tid;
+  // T
+  void* tkey;
+  void* tcols[2 * kMaxCols];
+  int64_t cap;
+  int64_t* d_count;
+};
+
+template <typename K>
+__device__ __forceinline__ uint32_t smem_slot(K k, int pbits) {
+  uint64_t h = KeyTraits<K>::hash64(k);
+  return (uint32_t)(h >> pbits) & (kSlots - 1);
+}
+
+// Compaction + materialisation of one probe tile. s_midx[i] is the matching
+// build row (index into the R-side source arrays, or into r_tid) or -1.
+template <typename K>
+__device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int tile_n, const K* s_key,
+                          const int32_t* s_midx, int32_t* s_pos, const JoinIO& io, uint64_t* tile_status,
+                          int* err, uint32_t* s_scan, uint64_t* s_base) {
+  const int t = threadIdx.x;
+  // blocked exclusive scan of match flags
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    int i = t * kItems + j;
+    cnt += (i < tile_n && s_midx[i] >= 0) ? 1u : 0u;
+  }
+  const int lane = t & 31, warp = t >> 5;
+  uint32_t x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_scan[warp] = x;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      uint32_t c = s_scan[w];
+      s_scan[w] = run;
+      run += c;
+    }
+    uint64_t excl = lookback_scan(tile_status, tile, run, err);
+    *s_base = excl;
+    if (tile == ntiles - 1 && io.d_count) *io.d_count = (int64_t)(excl + run);
+  }
+  __syncthreads();
+  uint32_t pos = s_scan[warp] + x - cnt;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    int i = t * kItems + j;
+    if (i < tile_n && s_midx[i] >= 0) s_pos[i] = (int32_t)pos++;
+  }
+  __syncthreads();
+  const int64_t base = (int64_t)*s_base;
+  const int64_t cap = io.cap;
+  bool overflow = false;
+  for (int i = t; i < tile_n; i += kThreads) {
+    if (s_midx[i] < 0) continue;
+    int64_t o = base + s_pos[i];
+    if (o >= cap) {
+      overflow = true;
+      continue;
+    }
+    ((K*)io.tkey)[o] = s_key[i];
+  }
+  if (overflow) set_status(err, GJ_ERR_CAPACITY);
+  for (int c = 0; c < io.nr_cols; ++c) {
+    for (int i = t; i < tile_n; i += kThreads) {
+      int32_t m = s_midx[i];
+      if (m < 0) continue;
+      int64_t o = base + s_pos[i];
+      if (o >= cap) continue;
+      int64_t src = io.r_tid ? io.r_tid[m] : m;
+      copy_elem(io.tcols[c], o, io.rsrc[c], src, io.rsize[c]);
+    }
+  }
+  for (int c = 0; c < io.ns_cols; ++c) {
+    for (int i = t; i < tile_n; i += kThreads) {
+      if (s_midx[i] < 0) continue;
+      int64_t o = base + s_pos[i];
+      if (o >= cap) continue;
+      int64_t src = io.s_tid ? io.s_tid[tile_base + i] : tile_base + i;
+      copy_elem(io.tcols[io.nr_cols + c], o, io.ssrc[c], src, io.ssize[c]);
+    }
+  }
+}
+
+template <typename K>
+constexpr size_t phj_smem_bytes() {
+  return (size_t)kTileS * sizeof(K) + 2 * (size_t)kTileS * 4 + (size_t)kSlots * 4 + (size_t)kBuildCap * sizeof(K);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) phj_probe_kernel(const K* __restrict__ rkey,
+                                                             const int64_t* __restrict__ roff, int pbits,
+                                                             const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                             uint64_t* tile_status, int* tile_counter, int64_t ntiles,
+                                                             int* err) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  K* s_key = (K*)s_raw;                                   // kTileS probe keys
+  int32_t* s_part = (int32_t*)(s_key + kTileS);           // partition of each probe row, later its output position
+  int32_t* s_midx = s_part + kTileS;                      // matching build row or -1
+  int32_t* s_slots = s_midx + kTileS;                     // table: build row + 1, 0 = empty
+  K* s_rkey = (K*)(s_slots + kSlots);                     // keys of the build chunk
+  __shared__ uint32_t s_scan[kThreads / 32];
+  __shared__ uint64_t s_base;
+  __shared__ int64_t s_tile;
+
+  const int t = threadIdx.x;
+  if (t == 0) s_tile = atomicAdd(tile_counter, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t tile_base = tile * kTileS;
+  const int tile_n = (int)min64(kTileS, ns - tile_base);
+  const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
+
+  for (int i = t; i < tile_n; i += kThreads) {
+    K k = skey[tile_base + i];
+    s_key[i] = k;
+    s_part[i] = (int32_t)((uint32_t)KeyTraits<K>::hash64(k) & pmask);
+    s_midx[i] = -1;
+  }
+  __syncthreads();
+
+  // walk the partitions present in this tile (non-decreasing in S')
+  int a = 0;
+  while (a < tile_n) {
+    const int32_t p = s_part[a];
+    int lo = a, hi = tile_n;  // first row with partition > p
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (s_part[mid] <= p) lo = mid + 1; else hi = mid;
+    }
+    const int b = lo;
+    const int64_t r_lo = roff[p], r_hi = roff[p + 1];
+    for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
+      const int cn = (int)min64(kBuildCap, r_hi - c0);
+      for (int j = t; j < kSlots; j += kThreads) s_slots[j] = 0;
+      __syncthreads();
+      for (int j = t; j < cn; j += kThreads) {
+        K k = rkey[c0 + j];
+        s_rkey[j] = k;
+        __threadfence_block();
+        uint32_t sl = smem_slot<K>(k, pbits);
+        for (int probe = 0; probe < kSlots; ++probe) {
+          int prev = atomicCAS(&s_slots[sl], 0, j + 1);
+          if (prev == 0) break;
+          if (s_rkey[prev - 1] == k) {
+            set_status(err, GJ_ERR_DUPLICATE_KEY);
+            break;
+          }
+          sl = (sl + 1) & (kSlots - 1);
+        }
+      }
+      __syncthreads();
+      for (int i = a + t; i < b; i += kThreads) {
+        K k = s_key[i];
+        uint32_t sl = smem_slot<K>(k, pbits);
+        for (int probe = 0; probe < kSlots; ++probe) {
+          int v = s_slots[sl];
+          if (v == 0) break;
+          if (s_rkey[v - 1] == k) {
+            if (s_midx[i] >= 0) set_status(err, GJ_ERR_DUPLICATE_KEY);
+            s_midx[i] = (int32_t)(c0 + v - 1);
+            break;
+          }
+          sl = (sl + 1) & (kSlots - 1);
+        }
+      }
+      __syncthreads();
+    }
+    a = b;
+  }
+  __syncthreads();
+  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_part, io, tile_status, err, s_scan, &s_base);
+}
+
+// ---------------------------------------------------------------- NPHJ
+template <typename K>
+__global__ void nphj_build_kernel(const K* __restrict__ rkey, int64_t nr, int32_t* __restrict__ ht, uint64_t mask,
+                                  int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+    K k = rkey[i];
+    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      int prev = atomicCAS(&ht[sl], 0, (int)(i + 1));
+      if (prev == 0) break;
+      if (rkey[prev - 1] == k) {
+        set_status(err, GJ_ERR_DUPLICATE_KEY);
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) nphj_probe_kernel(const K* __restrict__ rkey,
+                                                              const int32_t* __restrict__ ht, uint64_t mask,
+                                                              const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                              uint64_t* tile_status, int* tile_counter,
+                                                              int64_t ntiles, int* err) {
+  __shared__ K s_key[kTileS];
+  __shared__ int32_t s_pos[kTileS];
+  __shared__ int32_t s_midx[kTileS];
+  __shared__ uint32_t s_scan[kThreads / 32];
+  __shared__ uint64_t s_base;
+  __shared__ int64_t s_tile;
+  const int t = threadIdx.x;
+  if (t == 0) s_tile = atomicAdd(tile_counter, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t tile_base = tile * kTileS;
+  const int tile_n = (int)min64(kTileS, ns - tile_base);
+  for (int i = t; i < tile_n; i += kThreads) {
+    K k = skey[tile_base + i];
+    s_key[i] = k;
+    int32_t m = -1;
+    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      int v = ht[sl];
+      if (v == 0) break;
+      if (rkey[v - 1] == k) {
+        m = v - 1;
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+    s_midx[i] = m;
+  }
+  __syncthreads();
+  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
+}
+
+template <typename K>
+gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int variant, int bits, int bpp,
+                     gj_table* T, int64_t cap, int64_t* d_count) {
+  cudaStream_t s = ctx.stream;
+  Scratch scr(s);
+  gj_status st;
+  if ((st = cuda_check(cudaMemsetAsync(d_count, 0, sizeof(int64_t), s))) != GJ_OK) return st;
+  const int64_t nr = R->n, ns = S->n;
+  JoinIO io{};
+  io.nr_cols = R->ncols;
+  io.ns_cols = S->ncols;
+  io.tkey = T->key;
+  for (int c = 0; c < R->ncols + S->ncols; ++c) io.tcols[c] = T->cols[c];
+  io.cap = cap;
+  io.d_count = d_count;
+  for (int c = 0; c < R->ncols; ++c) io.rsize[c] = dtype_size(R->col_type[c]);
+  for (int c = 0; c < S->ncols; ++c) io.ssize[c] = dtype_size(S->col_type[c]);
+  if (ns == 0) return GJ_OK;
+
+  const int64_t ntiles = (ns + kTileS - 1) / kTileS;
+  uint64_t* tstat = scr.get_as<uint64_t>(ntiles);
+  int* counter = scr.get_as<int>(1);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = cuda_check(cudaMemsetAsync(tstat, 0, sizeof(uint64_t) * ntiles, s))) != GJ_OK) return st;
+  if ((st = cuda_check(cudaMemsetAsync(counter, 0, sizeof(int), s))) != GJ_OK) return st;
+
+  if (variant == GJ_JOIN_NPHJ) {
+    uint64_t slots = 1;
+    while (slots < (uint64_t)std::max<int64_t>(2 * nr, 2)) slots <<= 1;
+    int32_t* ht = scr.get_as<int32_t>(slots);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
+    for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+    for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+    if (nr > 0) {
+      int blocks = (int)std::min<int64_t>((nr + 255) / 256, (int64_t)ctx.num_sms * 16);
+      LaunchScope ls(ctx, KK_NPHJ_BUILD);
+      nphj_build_kernel<K><<<blocks, 256, 0, s>>>((const K*)R->key, nr, ht, slots - 1, ctx.d_status);
+    }
+    LaunchScope ls(ctx, KK_NPHJ_PROBE);
+    nphj_probe_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>((const K*)R->key, ht, slots - 1, (const K*)S->key,
+                                                                ns, io, tstat, counter, ntiles, ctx.d_status);
+    return cuda_check(cudaGetLastError());
+  }
+
+  // ---- partitioned hash joins
+  const bool gftr = variant == GJ_JOIN_PHJ_TR;
+  const K* rk = (const K*)R->key;
+  const K* sk = (const K*)S->key;
+  if (bits > 0) {
+    K* rk2 = scr.get_as<K>(std::max<int64_t>(nr, 1));
+    K* sk2 = scr.get_as<K>(ns);
+    ColSet rc{}, sc{};
+    if (gftr) {
+      rc.n = R->ncols;
+      for (int c = 0; c < R->ncols; ++c) {
+        rc.src[c] = R->cols[c];
+        rc.size[c] = dtype_size(R->col_type[c]);
+        rc.dst[c] = scr.get((size_t)std::max<int64_t>(nr, 1) * rc.size[c]);
+      }
+      sc.n = S->ncols;
+      for (int c = 0; c < S->ncols; ++c) {
+        sc.src[c] = S->cols[c];
+        sc.size[c] = dtype_size(S->col_type[c]);
+        sc.dst[c] = scr.get((size_t)ns * sc.size[c]);
+      }
+    } else {
+      rc.n = sc.n = 1;
+      rc.src[0] = sc.src[0] = nullptr;  // generated tuple ids
+      rc.size[0] = sc.size[0] = 4;
+      rc.dst[0] = scr.get((size_t)std::max<int64_t>(nr, 1) * 4);
+      sc.dst[0] = scr.get((size_t)ns * 4);
+    }
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, rk2, rc, nr, 0, bits, kHashed,
+                                  bpp)) != GJ_OK)
+      return st;
+    if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, sk, sk2, sc, ns, 0, bits, kHashed,
+                                  bpp)) != GJ_OK)
+      return st;
+    rk = rk2;
+    sk = sk2;
+    if (gftr) {
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = rc.dst[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = sc.dst[c];
+    } else {
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+      io.r_tid = (const int32_t*)rc.dst[0];
+      io.s_tid = (const int32_t*)sc.dst[0];
+    }
+  } else {
+    for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+    for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+  }
+  int64_t* roff = scr.get_as<int64_t>(((size_t)1 << bits) + 1);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, nr, 0, bits, kHashed, roff)) != GJ_OK)
+    return st;
+  const size_t dyn = phj_smem_bytes<K>();
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(K) == 8]) {
+    cudaFuncSetAttribute(phj_probe_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    attr_set[sizeof(K) == 8] = true;
+  }
+  LaunchScope ls(ctx, KK_PHJ_PROBE);
+  phj_probe_kernel<K><<<(unsigned)ntiles, kThreads, dyn, s>>>(rk, roff, bits, sk, ns, io, tstat, counter, ntiles,
+                                                               ctx.d_status);
+  return cuda_check(cudaGetLastError());
+}
+
+}  // namespace
+
+int choose_join_bits(int64_t nr, int64_t target) {
+  int bits = 0;
+  while (bits < 16 && (nr >> bits) > target) ++bits;
+  return bits;
+}
+
+gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,
+                   int64_t cap, int64_t* d_count) {
+  int variant = opt->join_variant;
+  if (variant == GJ_JOIN_AUTO) {
+    // Sec. 7: GFTR when the match ratio is >= 25 %, keys are skewed or 8 bytes wide;
+    // otherwise the GFUR partitioned join. Unknown hints read as the common case.
+    float mr = opt->match_ratio_hint < 0 ? 1.0f : opt->match_ratio_hint;
+    float z = opt->zipf_hint < 0 ? 0.0f : opt->zipf_hint;
+    variant = (mr >= 0.25f || z >= 0.5f || R->key_type == GJ_I64) ? GJ_JOIN_PHJ_TR : GJ_JOIN_PHJ_UR;
+  }
+  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 1024);
+  if (R->key_type == GJ_I64)
+    return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
+  return join_typed<int32_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
+}
+
+}  // namespace gj

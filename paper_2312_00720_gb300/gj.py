@@ -1,0 +1,270 @@
+"""Python binding of libgj (include/gj.h): argument marshalling only.
+
+Every entry point takes torch CUDA tensors, fills the C descriptors with their
+device pointers and calls the library on torch's current stream. Outputs are
+allocated with torch.empty on the same device. There is no fallback: if
+libgj.so is missing or fails to load, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgj.so")
+
+MAX_COLS = 8
+MAX_AGGS = 32
+I32, I64 = 0, 1
+AGG = {"sum": 0, "count": 1, "min": 2, "max": 3}
+JOIN = {"auto": 0, "phj_tr": 1, "phj_ur": 2, "nphj": 3}
+GROUPBY = {"auto": 0, "hgb": 1, "sgb": 2, "pgb": 3}
+STATUS = {0: "GJ_OK", 1: "GJ_ERR_INVALID_ARG", 2: "GJ_ERR_UNSUPPORTED", 3: "GJ_ERR_OOM", 4: "GJ_ERR_CAPACITY",
+          5: "GJ_ERR_DUPLICATE_KEY", 6: "GJ_ERR_TIMEOUT", 7: "GJ_ERR_CUDA"}
+
+
+class GjError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class Table(ctypes.Structure):
+    _fields_ = [("key_type", ctypes.c_int32), ("ncols", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("key", ctypes.c_void_p), ("col_type", ctypes.c_int32 * MAX_COLS),
+                ("cols", ctypes.c_void_p * MAX_COLS)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("join_variant", ctypes.c_int32), ("groupby_variant", ctypes.c_int32),
+                ("selector", ctypes.c_int32), ("radix_bits", ctypes.c_int32), ("bits_per_pass", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("sync", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("zipf_hint", ctypes.c_float), ("match_ratio_hint", ctypes.c_float),
+                ("groups_hint", ctypes.c_int64)]
+
+
+class ColRef(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int32), ("col", ctypes.c_int32), ("modulus", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load libgj.so (built by paper_2312_00720_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    p, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    lib.gj_options_default.argtypes = [P(Options)]
+    lib.gj_options_default.restype = None
+    lib.gj_status_string.argtypes = [i32]
+    lib.gj_status_string.restype = ctypes.c_char_p
+    lib.gj_get_device_status.argtypes = [p]
+    lib.gj_get_device_status.restype = i32
+    lib.gj_set_allocator.argtypes = [p, p, p]
+    lib.gj_set_allocator.restype = i32
+    lib.gj_radix_partition.argtypes = [P(Table), i32, i32, i32, P(Table), p, P(Options), p]
+    lib.gj_radix_partition.restype = i32
+    lib.gj_join.argtypes = [P(Table), P(Table), P(Options), P(Table), i64, p, p]
+    lib.gj_join.restype = i32
+    lib.gj_groupby.argtypes = [P(Table), i32, p, p, P(Options), p, p, i64, p, p]
+    lib.gj_groupby.restype = i32
+    lib.gj_join_groupby.argtypes = [P(Table), P(Table), ColRef, i32, p, p, P(Options), p, p, i64, p, p]
+    lib.gj_join_groupby.restype = i32
+    lib.gj_profile_enable.argtypes = [i32]
+    lib.gj_profile_enable.restype = None
+    lib.gj_profile_read.argtypes = [p, p, i32]
+    lib.gj_profile_read.restype = i32
+    lib.gj_kernel_name.argtypes = [i32]
+    lib.gj_kernel_name.restype = ctypes.c_char_p
+    lib.gj_kernel_launches.argtypes = []
+    lib.gj_kernel_launches.restype = i64
+    _lib = lib
+    return lib
+
+
+def profile_enable(on: bool):
+    """Record CUDA events around every library kernel launch on its stream."""
+    load().gj_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{kernel kind: (total ms, launches)} since the last read; synchronises the device."""
+    lib = load()
+    n = 32
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    k = lib.gj_profile_read(ms, cnt, n)
+    return {lib.gj_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k) if cnt[i]}
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(load().gj_kernel_launches())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.int64:
+        return I64
+    raise TypeError(f"unsupported dtype {t.dtype}: columns are int32 or int64")
+
+
+def _check_dev(t: torch.Tensor, n: int):
+    if not t.is_cuda:
+        raise ValueError("tensors must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    if t.numel() != n:
+        raise ValueError("all columns of a table must have the same length")
+
+
+def make_table(key: torch.Tensor, cols) -> Table:
+    cols = list(cols)
+    if len(cols) > MAX_COLS:
+        raise ValueError(f"at most {MAX_COLS} columns")
+    n = key.numel()
+    _check_dev(key, n)
+    t = Table()
+    t.key_type = _dtype_code(key)
+    t.ncols = len(cols)
+    t.n = n
+    t.key = key.data_ptr() if n else None
+    for c, col in enumerate(cols):
+        _check_dev(col, n)
+        t.col_type[c] = _dtype_code(col)
+        t.cols[c] = col.data_ptr() if n else None
+    return t
+
+
+def options(join: str = "auto", groupby: str = "auto", radix_bits: int = 0, bits_per_pass: int = 0,
+            sync: bool = True, zipf_hint: float = -1.0, match_ratio_hint: float = -1.0, groups_hint: int = 0,
+            selector: int = 0) -> Options:
+    o = Options()
+    load().gj_options_default(ctypes.byref(o))
+    o.join_variant = JOIN[join]
+    o.groupby_variant = GROUPBY[groupby]
+    o.radix_bits = radix_bits
+    o.bits_per_pass = bits_per_pass
+    o.sync = 1 if sync else 0
+    o.zipf_hint = zipf_hint
+    o.match_ratio_hint = match_ratio_hint
+    o.groups_hint = groups_hint
+    o.selector = selector
+    return o
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _raise(code: int, where: str):
+    if code != 0:
+        raise GjError(code, where)
+
+
+def device_status() -> int:
+    return load().gj_get_device_status(_stream())
+
+
+def radix_partition(key: torch.Tensor, cols, bit_lo: int, bit_hi: int, transform: int = 0,
+                    offsets: bool = False, bits_per_pass: int = 0, sync: bool = True):
+    """Stable radix-partition of (key, cols) on bits [bit_lo, bit_hi) of d(key) (Sec. 2.3)."""
+    lib = load()
+    cols = list(cols)
+    kin = make_table(key, cols)
+    kout_t = torch.empty_like(key)
+    cols_out = [torch.empty_like(c) for c in cols]
+    kout = make_table(kout_t, cols_out)
+    off = torch.empty((1 << (bit_hi - bit_lo)) + 1, dtype=torch.int64, device=key.device) if offsets else None
+    o = options(bits_per_pass=bits_per_pass, sync=sync)
+    _raise(lib.gj_radix_partition(ctypes.byref(kin), bit_lo, bit_hi, transform, ctypes.byref(kout),
+                                  None if off is None else off.data_ptr(), ctypes.byref(o), _stream()),
+           "gj_radix_partition")
+    return kout_t, cols_out, off
+
+
+def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | None = None,
+         radix_bits: int = 0, bits_per_pass: int = 0, sync: bool = True, out=None, count=None,
+         match_ratio_hint: float = -1.0, zipf_hint: float = -1.0):
+    """R join S on key (Sec. 2.2). Returns (T.key, [T.cols: R's then S's], device count tensor).
+
+    ``out`` may pass preallocated (key, cols) outputs and ``count`` a device int64[1]."""
+    lib = load()
+    R = make_table(rkey, rcols)
+    S = make_table(skey, scols)
+    if capacity is None:
+        capacity = skey.numel()
+    if out is None:
+        tkey = torch.empty(capacity, dtype=rkey.dtype, device=rkey.device)
+        tcols = [torch.empty(capacity, dtype=c.dtype, device=c.device) for c in list(rcols) + list(scols)]
+    else:
+        tkey, tcols = out
+    T = Table()
+    T.key_type = _dtype_code(tkey)
+    T.ncols = len(tcols)
+    T.n = capacity
+    T.key = tkey.data_ptr() if capacity else None
+    for c, col in enumerate(tcols):
+        T.col_type[c] = _dtype_code(col)
+        T.cols[c] = col.data_ptr() if capacity else None
+    if count is None:
+        count = torch.zeros(1, dtype=torch.int64, device=rkey.device)
+    o = options(join=variant, radix_bits=radix_bits, bits_per_pass=bits_per_pass, sync=sync,
+                match_ratio_hint=match_ratio_hint, zipf_hint=zipf_hint)
+    _raise(lib.gj_join(ctypes.byref(R), ctypes.byref(S), ctypes.byref(o), ctypes.byref(T), capacity,
+                       ctypes.c_void_p(count.data_ptr()), _stream()), "gj_join")
+    return tkey, tcols, count
+
+
+def _agg_arrays(aggs, n_out, device, capacity):
+    ops = (ctypes.c_int32 * len(aggs))(*[AGG[a] if isinstance(a, str) else int(a) for a in aggs])
+    outs = [torch.empty(capacity, dtype=torch.int64, device=device) for _ in aggs]
+    ptrs = (ctypes.c_void_p * len(aggs))(*[t.data_ptr() if capacity else None for t in outs])
+    return ops, outs, ptrs
+
+
+def groupby(key, vals, aggs, agg_cols, *, variant: str = "hgb", capacity: int | None = None,
+            radix_bits: int = 0, sync: bool = True, groups_hint: int = 0, zipf_hint: float = -1.0):
+    """GROUP BY key (Sec. 2.2, Alg. 1). Returns (keys, [int64 aggregate columns], device group count)."""
+    lib = load()
+    t = make_table(key, vals)
+    if capacity is None:
+        capacity = max(1, key.numel())
+    ops, outs, ptrs = _agg_arrays(aggs, capacity, key.device, capacity)
+    oc = (ctypes.c_int32 * len(aggs))(*[int(c) for c in agg_cols])
+    okeys = torch.empty(capacity, dtype=key.dtype, device=key.device)
+    ng = torch.zeros(1, dtype=torch.int64, device=key.device)
+    o = options(groupby=variant, radix_bits=radix_bits, sync=sync, groups_hint=groups_hint, zipf_hint=zipf_hint)
+    _raise(lib.gj_groupby(ctypes.byref(t), len(aggs), ops, oc, ctypes.byref(o), okeys.data_ptr(), ptrs, capacity,
+                          ctypes.c_void_p(ng.data_ptr()), _stream()), "gj_groupby")
+    return okeys, outs, ng
+
+
+def join_groupby(rkey, rcols, skey, scols, group_key, aggs, agg_cols, *, variant: str = "auto",
+                 capacity: int | None = None, radix_bits: int = 0, sync: bool = True):
+    """GROUP BY over R join S without materialising it. group_key / agg_cols are
+    (side, col, modulus) triples (side 0 = R, 1 = S; col -1 = join key)."""
+    lib = load()
+    R = make_table(rkey, rcols)
+    S = make_table(skey, scols)
+    if capacity is None:
+        capacity = max(1, skey.numel())
+    ops, outs, ptrs = _agg_arrays(aggs, capacity, rkey.device, capacity)
+    refs = (ColRef * len(aggs))(*[ColRef(int(s), int(c), int(m)) for s, c, m in agg_cols])
+    gk = ColRef(*[int(x) for x in group_key])
+    okeys = torch.empty(capacity, dtype=torch.int64, device=rkey.device)
+    ng = torch.zeros(1, dtype=torch.int64, device=rkey.device)
+    o = options(join=variant, radix_bits=radix_bits, sync=sync)
+    _raise(lib.gj_join_groupby(ctypes.byref(R), ctypes.byref(S), gk, len(aggs), ops, refs, ctypes.byref(o),
+                               okeys.data_ptr(), ptrs, capacity, ctypes.c_void_p(ng.data_ptr()), _stream()),
+           "gj_join_groupby")
+    return okeys, outs, ng
