@@ -171,7 +171,11 @@ def main():
     ap.add_argument("--variant", default="phj_tr", choices=["phj_tr", "phj_ur", "nphj"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--scale", type=int, default=0, help="divide |R| and |S| by 2^scale (profiling captures only)")
     args = ap.parse_args()
+    global NR, NS, MIN_BYTES
+    NR, NS = NR >> args.scale, NS >> args.scale
+    MIN_BYTES = (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

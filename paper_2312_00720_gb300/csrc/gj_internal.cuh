@@ -141,6 +141,39 @@ __device__ __forceinline__ void copy_elem(void* dst, int64_t o, const void* src,
     ((int32_t*)dst)[o] = ((const int32_t*)src)[i];
 }
 
+// ------------------------------------------------------------------ aggregates
+// Reducible aggregates (Sec. 2.2) in int64. SUM wraps in two's complement, so
+// every combination order gives the same bits.
+struct Aggs {
+  int32_t n;
+  int32_t op[kMaxAggs];
+  const void* src[kMaxAggs];  // value column of aggregate j (unused for COUNT)
+  int32_t size[kMaxAggs];     // 4 or 8
+  int64_t* out[kMaxAggs];
+};
+
+__host__ __device__ __forceinline__ int64_t agg_identity(int op) {
+  return op == GJ_AGG_MIN ? INT64_MAX : (op == GJ_AGG_MAX ? INT64_MIN : 0);
+}
+__device__ __forceinline__ int64_t agg_combine(int op, int64_t a, int64_t b) {
+  switch (op) {
+    case GJ_AGG_MIN: return a < b ? a : b;
+    case GJ_AGG_MAX: return a > b ? a : b;
+    default: return (int64_t)((uint64_t)a + (uint64_t)b);
+  }
+}
+// The value row `row` contributes to aggregate j (COUNT contributes 1).
+__device__ __forceinline__ int64_t agg_value(const Aggs& A, int j, int64_t row) {
+  return A.op[j] == GJ_AGG_COUNT ? 1 : load_as_i64(A.src[j], A.size[j], row);
+}
+__device__ __forceinline__ void agg_atomic(int op, int64_t* p, int64_t v) {
+  switch (op) {
+    case GJ_AGG_MIN: atomicMin((long long*)p, (long long)v); break;
+    case GJ_AGG_MAX: atomicMax((long long*)p, (long long)v); break;
+    default: atomicAdd((unsigned long long*)p, (unsigned long long)v); break;
+  }
+}
+
 // ------------------------------------------------------------------ host side
 struct Ctx {
   cudaStream_t stream;
