@@ -136,6 +136,11 @@ __device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int t
 }
 
 template <typename K>
+__device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict__ roff, int pbits,
+                           const K* __restrict__ skey, int64_t tile_base, int tile_n, K* s_key, int32_t* s_part,
+                           int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err);
+
+template <typename K>
 constexpr size_t phj_smem_bytes() {
   return (size_t)kTileS * sizeof(K) + 2 * (size_t)kTileS * 4 + (size_t)kSlots * 4 + (size_t)kBuildCap * sizeof(K);
 }
@@ -162,8 +167,19 @@ __global__ void __launch_bounds__(kThreads) phj_probe_kernel(const K* __restrict
   const int64_t tile = s_tile;
   const int64_t tile_base = tile * kTileS;
   const int tile_n = (int)min64(kTileS, ns - tile_base);
-  const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
+  probe_tile<K>(rkey, roff, pbits, skey, tile_base, tile_n, s_key, s_part, s_midx, s_slots, s_rkey, err);
+  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_part, io, tile_status, err, s_scan, &s_base);
+}
 
+// Finds, for every probe row of S'[tile_base, tile_base + tile_n), the build row
+// of R' with the same key (s_midx, -1 = none): one shared-memory table per build
+// partition (or per chunk of kBuildCap rows of it) present in the tile.
+template <typename K>
+__device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict__ roff, int pbits,
+                           const K* __restrict__ skey, int64_t tile_base, int tile_n, K* s_key, int32_t* s_part,
+                           int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err) {
+  const int t = threadIdx.x;
+  const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
   for (int i = t; i < tile_n; i += kThreads) {
     K k = skey[tile_base + i];
     s_key[i] = k;
@@ -222,7 +238,6 @@ __global__ void __launch_bounds__(kThreads) phj_probe_kernel(const K* __restrict
     a = b;
   }
   __syncthreads();
-  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_part, io, tile_status, err, s_scan, &s_base);
 }
 
 // ---------------------------------------------------------------- NPHJ
@@ -281,6 +296,227 @@ __global__ void __launch_bounds__(kThreads) nphj_probe_kernel(const K* __restric
   }
   __syncthreads();
   emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
+}
+
+// ---------------------------------------------------------------- join -> group-by
+// The group-by that follows a join (Sec. 1) fused into the probe: each match is
+// aggregated where it is found and T is never written. Groups live either in a
+// dense slot array indexed by the key's residue (the group key is `x % m`, so
+// it lies in (-m, m)) with per-block shared-memory pre-aggregation, or in a
+// global open-addressing table of int64 group keys.
+constexpr int64_t kEmptyKey = INT64_MIN;
+
+struct FusedRef {
+  int32_t is_key;  // the join key itself
+  int32_t side;    // 0 = R (indexed by the build-side match), 1 = S (by the probe row)
+  int32_t size;
+  int64_t mod;
+  const void* src;
+  const int32_t* tid;  // UR: ids carried through the partitioning
+};
+
+struct GroupSink {
+  int32_t dense;
+  int32_t smem;
+  int64_t dense_off;
+  int64_t nslots;  // dense domain or table capacity; table mode has one more slot for kEmptyKey
+  uint64_t mask;
+  int64_t* keys;
+  unsigned long long* cnt;  // matches per slot: a slot holds a group iff cnt > 0
+  int32_t nagg;
+  int32_t op[kMaxAggs];
+  int64_t* agg[kMaxAggs];
+  FusedRef gk;
+  FusedRef val[kMaxAggs];
+};
+
+__device__ __forceinline__ int64_t fused_value(const FusedRef& f, int64_t m, int64_t i, int64_t key) {
+  int64_t v;
+  if (f.is_key) {
+    v = key;
+  } else {
+    int64_t idx = f.side == 0 ? m : i;
+    if (f.tid) idx = f.tid[idx];
+    v = load_as_i64(f.src, f.size, idx);
+  }
+  return f.mod > 0 ? v % f.mod : v;
+}
+
+__device__ __forceinline__ int64_t sink_slot(const GroupSink& G, int64_t gk, int* err) {
+  if (G.dense) return gk + G.dense_off;
+  if (gk == kEmptyKey) return G.nslots;
+  uint64_t sl = fmix64((uint64_t)gk) & G.mask;
+  for (uint64_t probe = 0; probe <= G.mask; ++probe) {
+    int64_t cur = (int64_t)ld_volatile((const uint64_t*)&G.keys[sl]);
+    if (cur == gk) return (int64_t)sl;
+    if (cur == kEmptyKey) {
+      unsigned long long old = atomicCAS((unsigned long long*)&G.keys[sl], (unsigned long long)kEmptyKey,
+                                         (unsigned long long)gk);
+      if ((int64_t)old == kEmptyKey || (int64_t)old == gk) return (int64_t)sl;
+    }
+    sl = (sl + 1) & G.mask;
+  }
+  set_status(err, GJ_ERR_CAPACITY);
+  return -1;
+}
+
+// Aggregates one match (build index m, probe index i, join key) into the sink.
+__device__ __forceinline__ void sink_add(const GroupSink& G, int64_t m, int64_t i, int64_t key,
+                                         unsigned long long* s_cnt, int64_t* s_agg, int* err) {
+  const int64_t gk = fused_value(G.gk, m, i, key);
+  const int64_t sl = sink_slot(G, gk, err);
+  if (sl < 0) return;
+  if (G.smem) {
+    atomicAdd(&s_cnt[sl], 1ull);
+    for (int j = 0; j < G.nagg; ++j)
+      agg_atomic(G.op[j], &s_agg[(int64_t)j * G.nslots + sl],
+                 G.op[j] == GJ_AGG_COUNT ? 1 : fused_value(G.val[j], m, i, key));
+  } else {
+    atomicAdd(&G.cnt[sl], 1ull);
+    for (int j = 0; j < G.nagg; ++j)
+      agg_atomic(G.op[j], &G.agg[j][sl], G.op[j] == GJ_AGG_COUNT ? 1 : fused_value(G.val[j], m, i, key));
+  }
+}
+
+__device__ void sink_smem_init(const GroupSink& G, unsigned long long* s_cnt, int64_t* s_agg) {
+  if (!G.smem) return;
+  for (int64_t s = threadIdx.x; s < G.nslots; s += blockDim.x) {
+    s_cnt[s] = 0;
+    for (int j = 0; j < G.nagg; ++j) s_agg[(int64_t)j * G.nslots + s] = agg_identity(G.op[j]);
+  }
+  __syncthreads();
+}
+
+__device__ void sink_smem_flush(const GroupSink& G, const unsigned long long* s_cnt, const int64_t* s_agg) {
+  if (!G.smem) return;
+  __syncthreads();
+  for (int64_t s = threadIdx.x; s < G.nslots; s += blockDim.x) {
+    if (s_cnt[s] == 0) continue;
+    atomicAdd(&G.cnt[s], s_cnt[s]);
+    for (int j = 0; j < G.nagg; ++j) agg_atomic(G.op[j], &G.agg[j][s], s_agg[(int64_t)j * G.nslots + s]);
+  }
+}
+
+__global__ void sink_init_kernel(GroupSink G) {
+  const int64_t total = G.nslots + (G.dense ? 0 : 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total; s += stride) {
+    if (!G.dense) G.keys[s] = kEmptyKey;
+    G.cnt[s] = 0;
+    for (int j = 0; j < G.nagg; ++j) G.agg[j][s] = agg_identity(G.op[j]);
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) phj_probe_agg_kernel(const K* __restrict__ rkey,
+                                                                 const int64_t* __restrict__ roff, int pbits,
+                                                                 const K* __restrict__ skey, int64_t ns, GroupSink G,
+                                                                 int* tile_counter, int64_t ntiles, int* err) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  K* s_key = (K*)s_raw;
+  int32_t* s_part = (int32_t*)(s_key + kTileS);
+  int32_t* s_midx = s_part + kTileS;
+  int32_t* s_slots = s_midx + kTileS;
+  K* s_rkey = (K*)(s_slots + kSlots);
+  unsigned long long* s_cnt = (unsigned long long*)(s_rkey + kBuildCap);
+  int64_t* s_agg = (int64_t*)(s_cnt + (G.smem ? G.nslots : 0));
+  __shared__ int64_t s_tile;
+  sink_smem_init(G, s_cnt, s_agg);
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t tile_base = tile * kTileS;
+    const int tile_n = (int)min64(kTileS, ns - tile_base);
+    probe_tile<K>(rkey, roff, pbits, skey, tile_base, tile_n, s_key, s_part, s_midx, s_slots, s_rkey, err);
+    for (int i = threadIdx.x; i < tile_n; i += kThreads) {
+      const int32_t m = s_midx[i];
+      if (m >= 0) sink_add(G, m, tile_base + i, (int64_t)s_key[i], s_cnt, s_agg, err);
+    }
+    __syncthreads();
+  }
+  sink_smem_flush(G, s_cnt, s_agg);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) nphj_probe_agg_kernel(const K* __restrict__ rkey,
+                                                                  const int32_t* __restrict__ ht, uint64_t mask,
+                                                                  const K* __restrict__ skey, int64_t ns, GroupSink G,
+                                                                  int* err) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  unsigned long long* s_cnt = (unsigned long long*)s_raw;
+  int64_t* s_agg = (int64_t*)(s_cnt + (G.smem ? G.nslots : 0));
+  sink_smem_init(G, s_cnt, s_agg);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += stride) {
+    const K k = skey[i];
+    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      int v = ht[sl];
+      if (v == 0) break;
+      if (rkey[v - 1] == k) {
+        sink_add(G, v - 1, i, (int64_t)k, s_cnt, s_agg, err);
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+  }
+  sink_smem_flush(G, s_cnt, s_agg);
+}
+
+// Writes the occupied slots densely: out_keys / out_aggs[j], g = *d_ngroups.
+constexpr int kEmitItems = 8;
+constexpr int kEmitTile = kThreads * kEmitItems;
+
+__global__ void __launch_bounds__(kThreads) group_emit_kernel(GroupSink G, int64_t* __restrict__ out_keys,
+                                                              Aggs out, int64_t cap, int64_t* d_ngroups,
+                                                              uint64_t* tstat, int* counter, int64_t ntiles,
+                                                              int* err) {
+  __shared__ uint32_t s_scan[kThreads / 32];
+  __shared__ uint64_t s_base;
+  __shared__ int64_t s_tile;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = atomicAdd(counter, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t total = G.nslots + (G.dense ? 0 : 1);
+  const int64_t tb = tile * kEmitTile + (int64_t)t * kEmitItems;
+  uint32_t cnt = 0;
+  for (int r = 0; r < kEmitItems; ++r) cnt += (tb + r < total && G.cnt[tb + r] > 0) ? 1u : 0u;
+  uint32_t x = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_scan[warp] = x;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      uint32_t c = s_scan[w];
+      s_scan[w] = run;
+      run += c;
+    }
+    s_base = lookback_scan(tstat, tile, run, err);
+    if (tile == ntiles - 1) *d_ngroups = (int64_t)(s_base + run);
+  }
+  __syncthreads();
+  int64_t o = (int64_t)s_base + s_scan[warp] + x - cnt;
+  bool overflow = false;
+  for (int r = 0; r < kEmitItems; ++r) {
+    const int64_t sl = tb + r;
+    if (sl >= total || G.cnt[sl] == 0) continue;
+    if (o >= cap) {
+      overflow = true;
+      ++o;
+      continue;
+    }
+    out_keys[o] = G.dense ? sl - G.dense_off : (sl == G.nslots ? kEmptyKey : G.keys[sl]);
+    for (int j = 0; j < out.n; ++j) out.out[j][o] = G.agg[j][sl];
+    ++o;
+  }
+  if (overflow) set_status(err, GJ_ERR_CAPACITY);
 }
 
 template <typename K>
@@ -394,7 +630,192 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   return cuda_check(cudaGetLastError());
 }
 
+template <typename K>
+gj_status join_groupby_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int variant, int bits, int bpp,
+                             gj_colref gkref, int nagg, const int32_t* ops, const gj_colref* agg_cols,
+                             const gj_options* opt, int64_t* out_keys, int64_t* const* out_aggs, int64_t cap,
+                             int64_t* d_ngroups) {
+  cudaStream_t s = ctx.stream;
+  Scratch scr(s);
+  gj_status st;
+  if ((st = cuda_check(cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), s))) != GJ_OK) return st;
+  const int64_t nr = R->n, ns = S->n;
+  if (nr == 0 || ns == 0) return GJ_OK;
+  const int kt = sizeof(K) == 8 ? GJ_I64 : GJ_I32;
+
+  GroupSink G{};
+  G.nagg = nagg;
+  G.dense = gkref.modulus > 0 && gkref.modulus <= (int64_t(1) << 21);
+  if (G.dense) {
+    G.nslots = 2 * gkref.modulus - 1;
+    G.dense_off = gkref.modulus - 1;
+  } else {
+    int64_t est = opt->groups_hint > 0 ? std::min<int64_t>(opt->groups_hint, ns) : ns;
+    uint64_t c = 1;
+    while (c < (uint64_t)std::max<int64_t>(2, 2 * est)) c <<= 1;
+    G.nslots = (int64_t)c;
+    G.mask = c - 1;
+  }
+  const int64_t total = G.nslots + (G.dense ? 0 : 1);
+  const size_t smem_agg = (size_t)G.nslots * 8 * (nagg + 1);
+  G.smem = G.dense && smem_agg <= 96 * 1024;
+  G.cnt = scr.get_as<unsigned long long>(total);
+  if (!G.dense) G.keys = scr.get_as<int64_t>(total);
+  for (int j = 0; j < nagg; ++j) {
+    G.op[j] = ops[j];
+    G.agg[j] = scr.get_as<int64_t>(total);
+  }
+  int* counter = scr.get_as<int>(2);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = cuda_check(cudaMemsetAsync(counter, 0, 2 * sizeof(int), s))) != GJ_OK) return st;
+  {
+    LaunchScope ls(ctx, KK_AGG_INIT);
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx.num_sms * 8);
+    sink_init_kernel<<<std::max(blocks, 1), 256, 0, s>>>(G);
+  }
+
+  // columns the query reads on each side
+  bool need[2][kMaxCols] = {};
+  auto mark = [&](const gj_colref& c) {
+    if (c.col >= 0) need[c.side][c.col] = true;
+  };
+  mark(gkref);
+  for (int j = 0; j < nagg; ++j)
+    if (ops[j] != GJ_AGG_COUNT) mark(agg_cols[j]);
+  const void* src[2][kMaxCols];
+  for (int c = 0; c < R->ncols; ++c) src[0][c] = R->cols[c];
+  for (int c = 0; c < S->ncols; ++c) src[1][c] = S->cols[c];
+  const int32_t* tids[2] = {nullptr, nullptr};
+  const gj_table* side_tab[2] = {R, S};
+  const K* rk = (const K*)R->key;
+  const K* sk = (const K*)S->key;
+  int64_t* roff = nullptr;
+  int32_t* ht = nullptr;
+  uint64_t ht_slots = 0;
+
+  if (variant == GJ_JOIN_NPHJ) {
+    ht_slots = 1;
+    while (ht_slots < (uint64_t)std::max<int64_t>(2 * nr, 2)) ht_slots <<= 1;
+    ht = scr.get_as<int32_t>(ht_slots);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * ht_slots, s))) != GJ_OK) return st;
+    LaunchScope ls(ctx, KK_NPHJ_BUILD);
+    int blocks = (int)std::min<int64_t>((nr + 255) / 256, (int64_t)ctx.num_sms * 16);
+    nphj_build_kernel<K><<<blocks, 256, 0, s>>>(rk, nr, ht, ht_slots - 1, ctx.d_status);
+  } else {
+    const bool gftr = variant == GJ_JOIN_PHJ_TR;
+    if (bits > 0) {
+      for (int side = 0; side < 2; ++side) {
+        const gj_table* T = side_tab[side];
+        ColSet cs{};
+        int pos[kMaxCols];
+        if (gftr) {
+          for (int c = 0; c < T->ncols; ++c) {
+            if (!need[side][c]) continue;
+            pos[c] = cs.n;
+            cs.src[cs.n] = T->cols[c];
+            cs.size[cs.n] = dtype_size(T->col_type[c]);
+            cs.dst[cs.n] = scr.get((size_t)T->n * cs.size[cs.n]);
+            cs.n++;
+          }
+        } else {
+          cs.n = 1;
+          cs.src[0] = nullptr;
+          cs.size[0] = 4;
+          cs.dst[0] = scr.get((size_t)T->n * 4);
+        }
+        K* k2 = scr.get_as<K>(T->n);
+        if (scr.failed()) return GJ_ERR_OOM;
+        if ((st = radix_partition_run(ctx, scr, kt, T->key, k2, cs, T->n, 0, bits, kHashed, bpp)) != GJ_OK) return st;
+        if (side == 0)
+          rk = k2;
+        else
+          sk = k2;
+        if (gftr) {
+          for (int c = 0; c < T->ncols; ++c)
+            if (need[side][c]) src[side][c] = cs.dst[pos[c]];
+        } else {
+          tids[side] = (const int32_t*)cs.dst[0];
+        }
+      }
+    }
+    roff = scr.get_as<int64_t>(((size_t)1 << bits) + 1);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = partition_bounds_run(ctx, kt, rk, nr, 0, bits, kHashed, roff)) != GJ_OK) return st;
+  }
+
+  auto ref = [&](const gj_colref& c) {
+    FusedRef f{};
+    f.mod = c.modulus;
+    if (c.col < 0) {
+      f.is_key = 1;
+      return f;
+    }
+    f.side = c.side;
+    f.src = src[c.side][c.col];
+    f.size = dtype_size(side_tab[c.side]->col_type[c.col]);
+    f.tid = tids[c.side];
+    return f;
+  };
+  G.gk = ref(gkref);
+  for (int j = 0; j < nagg; ++j)
+    if (ops[j] != GJ_AGG_COUNT) G.val[j] = ref(agg_cols[j]);
+
+  const size_t agg_dyn = G.smem ? smem_agg : 0;
+  if (variant == GJ_JOIN_NPHJ) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(nphj_probe_agg_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      attr = true;
+    }
+    LaunchScope ls(ctx, KK_FUSED_PROBE);
+    int blocks = (int)std::min<int64_t>((ns + kThreads - 1) / kThreads, (int64_t)ctx.num_sms * 4);
+    nphj_probe_agg_kernel<K><<<blocks, kThreads, agg_dyn, s>>>(rk, ht, ht_slots - 1, sk, ns, G, ctx.d_status);
+  } else {
+    const int64_t ntiles = (ns + kTileS - 1) / kTileS;
+    const size_t dyn = phj_smem_bytes<K>() + agg_dyn;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(phj_probe_agg_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(phj_smem_bytes<K>() + 96 * 1024));
+      attr = true;
+    }
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phj_probe_agg_kernel<K>, kThreads, dyn);
+    int blocks = (int)std::min<int64_t>(ntiles, (int64_t)ctx.num_sms * std::max(per_sm, 1));
+    LaunchScope ls(ctx, KK_FUSED_PROBE);
+    phj_probe_agg_kernel<K><<<blocks, kThreads, dyn, s>>>(rk, roff, bits, sk, ns, G, counter, ntiles, ctx.d_status);
+  }
+
+  const int64_t etiles = (total + kEmitTile - 1) / kEmitTile;
+  uint64_t* tstat = scr.get_as<uint64_t>(etiles);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = cuda_check(cudaMemsetAsync(tstat, 0, sizeof(uint64_t) * etiles, s))) != GJ_OK) return st;
+  Aggs out{};
+  out.n = nagg;
+  for (int j = 0; j < nagg; ++j) out.out[j] = out_aggs[j];
+  LaunchScope ls(ctx, KK_GROUP_EMIT);
+  group_emit_kernel<<<(unsigned)etiles, kThreads, 0, s>>>(G, out_keys, out, cap, d_ngroups, tstat, counter + 1,
+                                                          etiles, ctx.d_status);
+  return cuda_check(cudaGetLastError());
+}
+
 }  // namespace
+
+gj_status join_groupby_run(const Ctx& ctx, const gj_table* R, const gj_table* S, gj_colref gk, int nagg,
+                           const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt, int64_t* out_keys,
+                           int64_t* const* out_aggs, int64_t cap, int64_t* d_ngroups) {
+  int variant = opt->join_variant;
+  // a global table on a build side of a few million rows stays in L2; larger
+  // build sides are partitioned
+  if (variant == GJ_JOIN_AUTO) variant = R->n <= (int64_t(1) << 22) ? GJ_JOIN_NPHJ : GJ_JOIN_PHJ_TR;
+  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 1024);
+  if (R->key_type == GJ_I64)
+    return join_groupby_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, gk, nagg, ops, agg_cols, opt,
+                                       out_keys, out_aggs, cap, d_ngroups);
+  return join_groupby_typed<int32_t>(ctx, R, S, variant, bits, opt->bits_per_pass, gk, nagg, ops, agg_cols, opt,
+                                     out_keys, out_aggs, cap, d_ngroups);
+}
 
 int choose_join_bits(int64_t nr, int64_t target) {
   int bits = 0;

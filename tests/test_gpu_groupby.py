@@ -1,0 +1,96 @@
+"""Group-by variants (HGB Alg. 1, SGB-TR, PGB-TR) through the C-ABI vs the oracle:
+canonically sorted (key, aggregates) rows must be identical."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_00720_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["hgb", "sgb", "pgb"]
+AGGS = ["count", "sum", "min", "max", "sum", "min", "max", "sum", "min", "max"]
+COLS = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
+
+
+def run_gb(gj, key, vals, aggs, cols, variant, **kw):
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    okeys, outs, ng = gj.groupby(dev(key), [dev(v) for v in vals], aggs, cols, variant=variant, **kw)
+    g = int(ng.item())
+    return np.stack([okeys[:g].cpu().numpy().astype(np.int64)] + [o[:g].cpu().numpy() for o in outs], 1) \
+        if g else np.zeros((0, 1 + len(aggs)), dtype=np.int64)
+
+
+def want_rows(key, vals, aggs, cols):
+    return oracle.canonical(oracle.groupby_sort(key, vals, aggs, cols))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n,g,kdt,theta", [
+    (0, 4, np.int32, 0.0), (1, 1, np.int32, 0.0), (31, 3, np.int32, 0.0), (511, 7, np.int64, 0.0),
+    (512, 512, np.int32, 0.0), (513, 10, np.int32, 0.0), (100000, 1, np.int32, 0.0),
+    (100000, 16, np.int32, 0.0), (100000, 4096, np.int64, 0.0), (200003, 1 << 17, np.int32, 0.0),
+    (300000, 1000, np.int32, 1.0), (300000, 1 << 20, np.int64, 1.0), (1 << 20, 1 << 22, np.int32, 0.0)])
+def test_groupby_matches_oracle(gj, variant, n, g, kdt, theta):
+    w = wl.groupby_workload(n, g, nvals=3, key_dtype=kdt, theta=theta, seed=n + g)
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], AGGS, COLS, variant))
+    want = want_rows(w["key"], w["vals"], AGGS, COLS)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_int64_values_and_negative_keys(gj, variant):
+    rng = np.random.default_rng(11)
+    n = 50000
+    key = rng.integers(-300, 300, n).astype(np.int32)
+    vals = [rng.integers(-(2**62), 2**62, n, dtype=np.int64), rng.integers(-(2**31), 2**31, n).astype(np.int32)]
+    aggs = ["sum", "min", "max", "count", "max", "min"]
+    cols = [0, 0, 0, 0, 1, 1]
+    got = oracle.canonical(run_gb(gj, key, vals, aggs, cols, variant))
+    assert np.array_equal(got, want_rows(key, vals, aggs, cols))
+
+
+def test_sgb_output_is_sorted_and_deterministic(gj):
+    w = wl.groupby_workload(200000, 5000, nvals=2, seed=2)
+    a = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], "sgb")
+    b = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], "sgb")
+    assert np.array_equal(a, b)
+    assert np.all(np.diff(a[:, 0]) > 0)
+
+
+def test_pgb_sub_rounds_when_partition_overflows(gj):
+    # one hashed bit gives partitions of ~100K distinct keys, far above one table
+    w = wl.groupby_workload(400000, 200000, nvals=1, seed=9)
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], ["count", "sum"], [0, 0], "pgb", radix_bits=1))
+    assert np.array_equal(got, want_rows(w["key"], w["vals"], ["count", "sum"], [0, 0]))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_capacity_overflow_is_reported(gj, variant):
+    w = wl.groupby_workload(10000, 1000, nvals=1, seed=3)
+    with pytest.raises(gj.GjError) as e:
+        run_gb(gj, w["key"], w["vals"], ["count"], [0], variant, capacity=10)
+    assert e.value.code == 4
+
+
+def test_auto_variant(gj):
+    w = wl.groupby_workload(100000, 64, nvals=1, seed=4)
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], ["sum"], [0], "auto"))
+    assert np.array_equal(got, want_rows(w["key"], w["vals"], ["sum"], [0]))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("g,kdt,theta", [(1 << 4, np.int32, 0.0), (1 << 12, np.int32, 0.0),
+                                          (1 << 20, np.int64, 0.0), (1 << 26, np.int32, 1.0)])
+def test_full_size_plain_groupby(gj, g, kdt, theta):
+    """2^27 rows, 3 int32 value columns in [-2^20, 2^20), COUNT + SUM/MIN/MAX per column;
+    all three variants equal the oracle's sort-based group-by exactly."""
+    n = 1 << 27
+    w = wl.groupby_workload(n, g, nvals=3, key_dtype=kdt, theta=theta, seed=77)
+    want = want_rows(w["key"], w["vals"], AGGS, COLS)
+    assert want[:, 1].sum() == n
+    for v in VARIANTS:
+        got = oracle.canonical(run_gb(gj, w["key"], w["vals"], AGGS, COLS, v))
+        assert np.array_equal(got, want), v
