@@ -174,6 +174,121 @@ gj_status gj_join_groupby(const gj_table* R, const gj_table* S, gj_colref group_
                           int64_t* out_keys, int64_t* const* out_aggs, int64_t capacity, int64_t* d_ngroups,
                           void* stream);
 
+/* ---- Batched execution ----------------------------------------------------
+ * Many join -> group-by queries (each as in gj_join_groupby) run in ONE
+ * persistent kernel launch that drains a device-side task queue: per query,
+ * tasks that clear its tables, build a hash table on R, probe S and aggregate
+ * each match into dense group slots, and write the groups out. Tasks are
+ * ordered so that every task's dependencies sit earlier in the queue; a task
+ * waits for them with a bounded spin (GJ_ERR_TIMEOUT if it gives up). The
+ * launch is captured once in a CUDA graph and replayed. The paper has no
+ * batched mode; each query computes exactly what gj_join_groupby computes.
+ *
+ * Restrictions of the batched path: int32 keys; group_key.modulus in
+ * [1, 2^20] (groups are the residues, read as dense slots); at most
+ * GJ_BATCH_MAX_AGGS aggregates per query. Column and output pointers are
+ * device memory that must stay valid and at the same address for the life of
+ * the plan; every launch recomputes all outputs from the current input
+ * contents. */
+#define GJ_BATCH_MAX_AGGS 8
+
+typedef struct {
+  gj_table R;
+  gj_table S;
+  gj_colref group_key;
+  int32_t nagg;
+  int32_t ops[GJ_BATCH_MAX_AGGS];
+  gj_colref agg_cols[GJ_BATCH_MAX_AGGS];
+  int64_t* out_keys;                       /* device int64, capacity rows */
+  int64_t* out_aggs[GJ_BATCH_MAX_AGGS];    /* device int64 each */
+  int64_t capacity;
+  int64_t* d_ngroups;                      /* device int64 */
+} gj_query;
+
+typedef struct gj_batch_plan gj_batch_plan;
+
+/* Tuning knobs of a batch plan; zero fields mean "let the autotuner choose".
+ * build_rows / probe_rows: rows per build / probe task; lookahead: how many
+ * queries ahead their clear+build tasks are queued before a query's probe
+ * tasks; blocks_per_sm: resident CTAs of the persistent kernel per SM. */
+typedef struct {
+  int32_t build_rows;
+  int32_t probe_rows;
+  int32_t lookahead;
+  int32_t blocks_per_sm;
+} gj_batch_config;
+
+/* Validates the queries, uploads the task queue, allocates the workspace,
+ * runs the autotuner for the zero fields of *cfg (cfg may be NULL: all
+ * tuned; the tuner times each candidate on this batch and keeps the fastest;
+ * results are cached per device and batch shape), and captures the chosen
+ * configuration in a CUDA graph. `stream` is used for tuning and set-up. */
+gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_config* cfg,
+                          gj_batch_plan** plan, void* stream);
+/* Replays the captured graph on `stream`: all nq queries, asynchronously. */
+gj_status gj_batch_launch(gj_batch_plan* plan, void* stream);
+/* The configuration the plan runs with. */
+gj_status gj_batch_get_config(const gj_batch_plan* plan, gj_batch_config* cfg);
+/* Frees the plan, its graph and workspace (synchronises the device). */
+gj_status gj_batch_destroy(gj_batch_plan* plan);
+
+/* ---- Learned variant selector ---------------------------------------------
+ * A multi-layer perceptron x(12) -> 64 -> ReLU -> 64 -> ReLU -> y(6), FP32,
+ * predicting log run time of the join variants PHJ-TR, PHJ-UR, NPHJ (y0..y2)
+ * and the group-by variants HGB, SGB, PGB (y3..y5). The paper chooses variants
+ * with cost models and heuristics (Sec. 4.1.3, 4.1.4, 4.4, 5.1.9, Fig.
+ * groupby-dt); the network has no counterpart there and those rules remain the
+ * fallback. Parameters are one float array of GJ_MLP_PARAMS values, row-major
+ * [out][in] weights each followed by its bias: w1[64][12] b1[64] w2[64][64]
+ * b2[64] w3[6][64] b3[6]. All pointers below are device memory; all calls are
+ * asynchronous on `stream`. */
+#define GJ_MLP_IN 12
+#define GJ_MLP_HIDDEN 64
+#define GJ_MLP_OUT 6
+#define GJ_MLP_PARAMS 5382
+
+/* y[batch][6] = f(theta, x[batch][12]). */
+gj_status gj_mlp_forward(const float* theta, const float* x, int32_t batch, float* y, void* stream);
+/* loss = (1/batch) sum_b sum_o mask[b][o] (y[b][o] - t[b][o])^2 and its gradient
+ * grad[GJ_MLP_PARAMS] (overwritten). Reductions run in a fixed order, so the
+ * result is identical on every run. batch >= 1. */
+gj_status gj_mlp_loss_grad(const float* theta, const float* x, const float* t, const float* mask, int32_t batch,
+                           float* grad, float* loss, void* stream);
+/* Adam (Kingma & Ba) with bias correction; step counts from 1; m, v are state
+ * arrays of GJ_MLP_PARAMS floats, zero before the first step. */
+gj_status gj_mlp_adam_step(float* theta, const float* grad, float* m, float* v, int32_t step, float lr, float beta1,
+                           float beta2, float eps, void* stream);
+/* theta -= lr * grad. */
+gj_status gj_mlp_sgd_step(float* theta, const float* grad, float lr, void* stream);
+/* For each of n feature rows (already normalised), the argmin of y0..y2 as a
+ * gj_join_variant (1 + index) and of y3..y5 as a gj_groupby_variant. */
+gj_status gj_mlp_select(const float* theta, const float* x, int32_t n, int32_t* join_variant, int32_t* gb_variant,
+                        void* stream);
+
+/* Selector used by gj_join / gj_groupby when a variant is AUTO and
+ * options.selector = GJ_SELECT_MLP. host_theta: GJ_MLP_PARAMS floats (host);
+ * mean / stdev: GJ_MLP_IN floats (host) normalising the raw features
+ * (x - mean) / stdev. Passing NULL theta removes the network, and AUTO falls
+ * back to the paper's rules. The raw features of a query are
+ *   0 log2(|R|+1)  1 log2(|S|+1)  2 key bytes  3 R payload columns
+ *   4 S payload columns  5 Zipf factor  6 match ratio  7 log2(groups+1)
+ *   8 aggregates  9 log2((|R|+1)/(|S|+1))  10 payload bytes per S row
+ *   11 log2(groups+1) / log2(|S|+2)
+ * with options' hints standing in for unknown skew, match ratio and groups. */
+gj_status gj_selector_set(const float* host_theta, const float* mean, const float* stdev);
+/* The variants AUTO would run under the paper's rules (GJ_SELECT_HEURISTIC):
+ * for the join, Sec. 7 (GFTR partitioned join if the match ratio is >= 25 %,
+ * the foreign keys are skewed or keys are 8 bytes, else the GFUR partitioned
+ * join); for the group-by, Fig. groupby-dt without a mandated sort (HGB when
+ * the expected groups' aggregates fit in shared memory, else the sort-based
+ * variant under high skew, else PGB-TR). Only sizes, types and options are read:
+ * the column pointers of R and S may be NULL. `S` is the group-by input. */
+gj_status gj_heuristic_choose(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt,
+                              int32_t* join_variant, int32_t* gb_variant);
+/* Writes the 12 raw features of a query into out[12] (host). Either table may be
+ * NULL when only one operator is chosen. */
+gj_status gj_query_features(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt, float* out);
+
 /* ---- Measurement support (no counterpart in the paper) -------------------
  * gj_profile_enable(1) makes every kernel launch of the library record a CUDA
  * event before and after itself on its stream; gj_profile_read synchronises the

@@ -329,6 +329,25 @@ gj_status gj_join_groupby(const gj_table* R, const gj_table* S, gj_colref group_
   return finish(ctx, opt, st);
 }
 
+gj_status gj_heuristic_choose(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt,
+                              int32_t* join_variant, int32_t* gb_variant) {
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (join_variant) {
+    if (!R) return GJ_ERR_INVALID_ARG;
+    *join_variant = heuristic_join_variant(R, opt);
+  }
+  if (gb_variant) {
+    if (!S || nagg < 1) return GJ_ERR_INVALID_ARG;
+    int dev = 0, smem = 200 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaGetLastError();
+    *gb_variant = choose_groupby_variant(S, nagg, nullptr, opt, std::min(smem, 200 * 1024));
+  }
+  return GJ_OK;
+}
+
 void gj_profile_enable(int32_t on) { g_timing.store(on ? 1 : 0); }
 
 int32_t gj_profile_read(double* ms, int64_t* launches, int32_t max_kinds) {

@@ -265,6 +265,14 @@ gj_status join_groupby_run(const Ctx& ctx, const gj_table* R, const gj_table* S,
                            const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt, int64_t* out_keys,
                            int64_t* const* out_aggs, int64_t cap, int64_t* d_ngroups);
 
+// The paper's rules (Sec. 7 for the join, Fig. groupby-dt for the group-by).
+int heuristic_join_variant(const gj_table* R, const gj_options* opt);
+int choose_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt, int smem_budget);
+
+// Learned selector: raw query features, and the network's choice (0 = no network).
+void query_features(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, float* f);
+int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join);
+
 // Total partition bits for a build side of nr rows so that a partition holds
 // about `target` rows; at most 16 bits (two passes of 8).
 int choose_join_bits(int64_t nr, int64_t target);

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kPgbThreads) pgb_kernel(const K* __restrict__ 
   int64_t* s_agg = (int64_t*)s_raw;                       // kPgbCap aggregates
   int32_t* s_slots = (int32_t*)(s_agg + kPgbCap);         // table: local id + 1
   K* s_keys = (K*)(s_slots + kPgbSlots);                  // distinct keys by local id
-  __shared__ int s_count, s_over, s_q;
+  __shared__ int s_count, s_over;
   __shared__ int64_t s_part, s_goff;
   __shared__ int64_t s_red[kPgbThreads / 32];
 
@@ -723,7 +723,7 @@ int choose_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, con
   // expected groups fit in shared memory, else PGB-TR unless the keys are
   // highly skewed (z >= 1), where the sort-based variant is taken.
   int64_t bytes = 0;
-  for (int j = 0; j < nagg; ++j) bytes += ops[j] == GJ_AGG_SUM ? 8 : 4;
+  for (int j = 0; j < nagg; ++j) bytes += (!ops || ops[j] == GJ_AGG_SUM) ? 8 : 4;
   int64_t g = opt->groups_hint > 0 ? opt->groups_hint : in->n;
   if (g * bytes <= smem_budget) return GJ_GB_HGB;
   if (opt->zipf_hint >= 1.0f) return GJ_GB_SGB;
@@ -734,6 +734,7 @@ gj_status groupby_run(const Ctx& ctx, const gj_table* in, int nagg, const int32_
                       const gj_options* opt, void* out_keys, int64_t* const* out_aggs, int64_t cap,
                       int64_t* d_ngroups) {
   int variant = opt->groupby_variant;
+  if (variant == GJ_GB_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(nullptr, in, nagg, opt, false);
   if (variant == GJ_GB_AUTO) variant = choose_groupby_variant(in, nagg, ops, opt, std::min(ctx.smem_optin, 200 * 1024));
   if (in->key_type == GJ_I64)
     return groupby_typed<int64_t>(ctx, in, nagg, ops, op_col, opt, variant, out_keys, out_aggs, cap, d_ngroups);

@@ -101,36 +101,65 @@ __device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int t
     if (i < tile_n && s_midx[i] >= 0) s_pos[i] = (int32_t)pos++;
   }
   __syncthreads();
+  // Each thread owns rows t, t + kThreads, ...: outputs of a warp are contiguous.
+  // All loads of a column are issued before its stores, so a thread keeps
+  // kItems gathers in flight instead of waiting on one at a time.
   const int64_t base = (int64_t)*s_base;
   const int64_t cap = io.cap;
+  int64_t o[kItems], ridx[kItems], sidx[kItems];
+  bool ok[kItems];
   bool overflow = false;
-  for (int i = t; i < tile_n; i += kThreads) {
-    if (s_midx[i] < 0) continue;
-    int64_t o = base + s_pos[i];
-    if (o >= cap) {
-      overflow = true;
-      continue;
-    }
-    ((K*)io.tkey)[o] = s_key[i];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int i = t + j * kThreads;
+    const int32_t m = i < tile_n ? s_midx[i] : -1;
+    o[j] = m >= 0 ? base + s_pos[i] : 0;
+    ok[j] = m >= 0 && o[j] < cap;
+    overflow |= m >= 0 && o[j] >= cap;
+    ridx[j] = m;
+    sidx[j] = tile_base + i;
   }
   if (overflow) set_status(err, GJ_ERR_CAPACITY);
-  for (int c = 0; c < io.nr_cols; ++c) {
-    for (int i = t; i < tile_n; i += kThreads) {
-      int32_t m = s_midx[i];
-      if (m < 0) continue;
-      int64_t o = base + s_pos[i];
-      if (o >= cap) continue;
-      int64_t src = io.r_tid ? io.r_tid[m] : m;
-      copy_elem(io.tcols[c], o, io.rsrc[c], src, io.rsize[c]);
-    }
+  if (io.r_tid) {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+      if (ok[j]) ridx[j] = __ldg(io.r_tid + ridx[j]);
   }
-  for (int c = 0; c < io.ns_cols; ++c) {
-    for (int i = t; i < tile_n; i += kThreads) {
-      if (s_midx[i] < 0) continue;
-      int64_t o = base + s_pos[i];
-      if (o >= cap) continue;
-      int64_t src = io.s_tid ? io.s_tid[tile_base + i] : tile_base + i;
-      copy_elem(io.tcols[io.nr_cols + c], o, io.ssrc[c], src, io.ssize[c]);
+  if (io.s_tid) {
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+      if (ok[j]) sidx[j] = __ldcs(io.s_tid + sidx[j]);
+  }
+  {
+    K* __restrict__ tk = (K*)io.tkey;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j)
+      if (ok[j]) __stcs(tk + o[j], s_key[t + j * kThreads]);
+  }
+  for (int c = 0; c < io.nr_cols + io.ns_cols; ++c) {
+    const bool rside = c < io.nr_cols;
+    const void* src = rside ? io.rsrc[c] : io.ssrc[c - io.nr_cols];
+    const int size = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
+    if (size == 8) {
+      const int64_t* __restrict__ s8 = (const int64_t*)src;
+      int64_t* __restrict__ d8 = (int64_t*)io.tcols[c];
+      int64_t v[kItems];
+#pragma unroll
+      for (int j = 0; j < kItems; ++j)
+        if (ok[j]) v[j] = rside ? __ldg(s8 + ridx[j]) : __ldcs(s8 + sidx[j]);
+#pragma unroll
+      for (int j = 0; j < kItems; ++j)
+        if (ok[j]) __stcs(d8 + o[j], v[j]);
+    } else {
+      const int32_t* __restrict__ s4 = (const int32_t*)src;
+      int32_t* __restrict__ d4 = (int32_t*)io.tcols[c];
+      int32_t v[kItems];
+#pragma unroll
+      for (int j = 0; j < kItems; ++j)
+        if (ok[j]) v[j] = rside ? __ldg(s4 + ridx[j]) : __ldcs(s4 + sidx[j]);
+#pragma unroll
+      for (int j = 0; j < kItems; ++j)
+        if (ok[j]) __stcs(d4 + o[j], v[j]);
     }
   }
 }
@@ -146,7 +175,7 @@ constexpr size_t phj_smem_bytes() {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads) phj_probe_kernel(const K* __restrict__ rkey,
+__global__ void __launch_bounds__(kThreads, 3) phj_probe_kernel(const K* __restrict__ rkey,
                                                              const int64_t* __restrict__ roff, int pbits,
                                                              const K* __restrict__ skey, int64_t ns, JoinIO io,
                                                              uint64_t* tile_status, int* tile_counter, int64_t ntiles,
@@ -180,8 +209,9 @@ __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict
                            int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err) {
   const int t = threadIdx.x;
   const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
+#pragma unroll 8
   for (int i = t; i < tile_n; i += kThreads) {
-    K k = skey[tile_base + i];
+    K k = __ldcs(skey + tile_base + i);
     s_key[i] = k;
     s_part[i] = (int32_t)((uint32_t)KeyTraits<K>::hash64(k) & pmask);
     s_midx[i] = -1;
@@ -202,11 +232,12 @@ __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict
     for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
       const int cn = (int)min64(kBuildCap, r_hi - c0);
       for (int j = t; j < kSlots; j += kThreads) s_slots[j] = 0;
+      // stage the chunk's keys first so the loads overlap, then insert
+#pragma unroll 8
+      for (int j = t; j < cn; j += kThreads) s_rkey[j] = __ldg(rkey + c0 + j);
       __syncthreads();
       for (int j = t; j < cn; j += kThreads) {
-        K k = rkey[c0 + j];
-        s_rkey[j] = k;
-        __threadfence_block();
+        const K k = s_rkey[j];
         uint32_t sl = smem_slot<K>(k, pbits);
         for (int probe = 0; probe < kSlots; ++probe) {
           int prev = atomicCAS(&s_slots[sl], 0, j + 1);
@@ -278,19 +309,41 @@ __global__ void __launch_bounds__(kThreads) nphj_probe_kernel(const K* __restric
   const int64_t tile = s_tile;
   const int64_t tile_base = tile * kTileS;
   const int tile_n = (int)min64(kTileS, ns - tile_base);
-  for (int i = t; i < tile_n; i += kThreads) {
-    K k = skey[tile_base + i];
-    s_key[i] = k;
+  // first probe of every owned row issued together; collisions continue serially
+  K k[kItems];
+  uint64_t sl[kItems];
+  int v[kItems];
+  K rk[kItems];
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int i = t + j * kThreads;
+    k[j] = i < tile_n ? __ldcs(skey + tile_base + i) : K(0);
+  }
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int i = t + j * kThreads;
+    sl[j] = KeyTraits<K>::hash64(k[j]) & mask;
+    v[j] = i < tile_n ? __ldg(ht + sl[j]) : 0;
+  }
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) rk[j] = v[j] ? __ldg(rkey + v[j] - 1) : K(0);
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int i = t + j * kThreads;
+    if (i >= tile_n) continue;
+    s_key[i] = k[j];
     int32_t m = -1;
-    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
-    for (uint64_t probe = 0; probe <= mask; ++probe) {
-      int v = ht[sl];
-      if (v == 0) break;
-      if (rkey[v - 1] == k) {
-        m = v - 1;
+    int vv = v[j];
+    K kk = rk[j];
+    uint64_t s2 = sl[j];
+    for (uint64_t probe = 0; probe <= mask && vv != 0; ++probe) {
+      if (kk == k[j]) {
+        m = vv - 1;
         break;
       }
-      sl = (sl + 1) & mask;
+      s2 = (s2 + 1) & mask;
+      vv = ht[s2];
+      if (vv) kk = rkey[vv - 1];
     }
     s_midx[i] = m;
   }
@@ -408,7 +461,7 @@ __global__ void sink_init_kernel(GroupSink G) {
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads) phj_probe_agg_kernel(const K* __restrict__ rkey,
+__global__ void __launch_bounds__(kThreads, 2) phj_probe_agg_kernel(const K* __restrict__ rkey,
                                                                  const int64_t* __restrict__ roff, int pbits,
                                                                  const K* __restrict__ skey, int64_t ns, GroupSink G,
                                                                  int* tile_counter, int64_t ntiles, int* err) {
@@ -823,16 +876,21 @@ int choose_join_bits(int64_t nr, int64_t target) {
   return bits;
 }
 
+int heuristic_join_variant(const gj_table* R, const gj_options* opt) {
+  // Sec. 7: GFTR when the match ratio is >= 25 %, the foreign keys are skewed or
+  // keys are 8 bytes wide; otherwise the GFUR partitioned join. Unknown hints
+  // read as the common case (all rows match, no skew); "skewed" is read as a
+  // Zipf factor of at least 0.5.
+  const float mr = opt->match_ratio_hint < 0 ? 1.0f : opt->match_ratio_hint;
+  const float z = opt->zipf_hint < 0 ? 0.0f : opt->zipf_hint;
+  return (mr >= 0.25f || z >= 0.5f || R->key_type == GJ_I64) ? GJ_JOIN_PHJ_TR : GJ_JOIN_PHJ_UR;
+}
+
 gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,
                    int64_t cap, int64_t* d_count) {
   int variant = opt->join_variant;
-  if (variant == GJ_JOIN_AUTO) {
-    // Sec. 7: GFTR when the match ratio is >= 25 %, keys are skewed or 8 bytes wide;
-    // otherwise the GFUR partitioned join. Unknown hints read as the common case.
-    float mr = opt->match_ratio_hint < 0 ? 1.0f : opt->match_ratio_hint;
-    float z = opt->zipf_hint < 0 ? 0.0f : opt->zipf_hint;
-    variant = (mr >= 0.25f || z >= 0.5f || R->key_type == GJ_I64) ? GJ_JOIN_PHJ_TR : GJ_JOIN_PHJ_UR;
-  }
+  if (variant == GJ_JOIN_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(R, S, 0, opt, true);
+  if (variant == GJ_JOIN_AUTO) variant = heuristic_join_variant(R, opt);
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 1024);
   if (R->key_type == GJ_I64)
     return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);

@@ -2,12 +2,21 @@
 // number of payload columns on bits [lo, hi) of the key, partitions stored
 // contiguously. One read of the keys builds the digit histogram of every pass
 // (the paper's "histogram pass"); then each pass of <= 8 bits reads key and
-// columns once and writes them once, sequentially, in tiles that are ranked
-// stably in shared memory and placed with a decoupled look-back over tiles.
+// columns once and writes them once, sequentially.
+//
+// A pass works on tiles taken in order from an atomic counter. Thread 0 of a
+// block issues bulk asynchronous copies (cp.async.bulk, completion on an
+// mbarrier) of the tile's key and every payload column into shared memory, so a
+// whole tile is in flight at once. Keys are ranked stably per warp with
+// match.any (the warp's rows are contiguous, lanes in row order); per-digit warp
+// counts give each row its position inside the tile's digit-sorted order, and a
+// decoupled look-back over tiles (one 32-bit word per tile and digit: 2-bit flag,
+// 30-bit count) gives the global offset of the tile's run of every digit. Every
+// column is then written in sorted order through an inverse index, so warps
+// store contiguous runs of each digit.
 //
 // Moving every payload column with the key in the same pass is what the GFTR
-// pattern needs (Sec. 4.1.2): all columns land in the same positions because
-// one rank computation drives all of them.
+// pattern needs (Sec. 4.1.2): one rank computation places all columns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,13 +28,13 @@ namespace gj {
 namespace {
 
 constexpr int kRadixMax = 256;
-constexpr int kScatterThreads = 256;
-constexpr int kScatterItems = 16;
-constexpr int kTile = kScatterThreads * kScatterItems;
-constexpr int kWarps = kScatterThreads / 32;
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxChunks = 16;  // 32-row chunks per warp: tiles of up to 8192 rows
 constexpr uint32_t kSFlagAgg = 1u << 30;
 constexpr uint32_t kSFlagInc = 2u << 30;
 constexpr uint32_t kSVal = (1u << 30) - 1;
+constexpr int kSmemBudget = 100 * 1024;  // in-stage + per-row arrays; two blocks per SM
 
 struct PassDigits {
   int passes;
@@ -33,8 +42,46 @@ struct PassDigits {
   int width[16];
 };
 
-// Exclusive scan of one value per thread over a 256-thread block.
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: after kSpinLimit polls the error is recorded and the caller
+// proceeds, so the kernel always ends.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t phase, int* err) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, phase)) {
+    if (++spins > kSpinLimit) {
+      set_status(err, GJ_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
+// Exclusive scan of one value per thread over the block.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -55,11 +102,11 @@ __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_w
   }
   __syncthreads();
   uint32_t before = warp ? s_warp[warp - 1] : 0;
-  if (total) *total = s_warp[kWarps - 1];
   __syncthreads();
   return before + x - v;
 }
 
+// ---------------------------------------------------------------- histogram
 template <typename K>
 __global__ void __launch_bounds__(256) radix_hist_kernel(const K* __restrict__ kin, int64_t n, PassDigits pd,
                                                          int transform, uint32_t* __restrict__ hist) {
@@ -75,7 +122,8 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const K* __restrict__ k
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   auto count = [&](K k) {
-    for (int q = 0; q < pd.passes; ++q) atomicAdd(&sh[q][extract_digit<K>(k, transform, pd.shift[q], pd.width[q])], 1u);
+    for (int q = 0; q < pd.passes; ++q)
+      atomicAdd(&sh[q][extract_digit<K>(k, transform, pd.shift[q], pd.width[q])], 1u);
   };
   const uint4* body = reinterpret_cast<const uint4*>(kin + head);
   for (int64_t v = tid; v < nvec; v += stride) {
@@ -93,103 +141,150 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(const K* __restrict__ k
   }
 }
 
+// ---------------------------------------------------------------- scatter
+struct ScatterArgs {
+  const void* kin;
+  void* kout;
+  ColSet cols;
+  uint32_t gen_mask;  // columns whose values are the input row index (tuple ids)
+  int64_t n;
+  int shift, width, transform;
+  const uint32_t* hist;  // 2^width global digit counts of this pass
+  uint32_t* status;      // tiles x 2^width look-back words
+  int* tile_counter;
+  int* err;
+  int tile_rows;  // 512 * chunks
+  int chunks;     // 32-row chunks per warp
+  int bulk;       // 1: every source is 16-byte aligned, copy with cp.async.bulk
+  int32_t col_off[kMaxCols];  // byte offset of each column's stage in shared memory (key at 0)
+  int32_t inv_off, sdig_off, wcnt_off;
+};
+
 template <typename T>
-__device__ __forceinline__ void scatter_column(const T* __restrict__ src, T* __restrict__ dst, bool gen_tid,
-                                               int64_t seg, int lane, const uint32_t* spos, int nvalid_mask_items,
-                                               int64_t n, T* staging, const int64_t* s_gdst, const uint8_t* s_sdig,
-                                               int tile_n, int64_t tile_base) {
-#pragma unroll
-  for (int i = 0; i < kScatterItems; ++i) {
-    int64_t row = seg + i * 32 + lane;
-    if (row < n) {
-      T v = gen_tid ? (T)row : src[row];
-      staging[spos[i]] = v;
-    }
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < tile_n; p += kScatterThreads) dst[s_gdst[s_sdig[p]] + p] = staging[p];
-  __syncthreads();
+__device__ __forceinline__ void stage_tail(unsigned char* stage, const T* src, int64_t tile_base, int tile_n,
+                                           int from) {
+  for (int r = from + threadIdx.x; r < tile_n; r += kThreads) ((T*)stage)[r] = src[tile_base + r];
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kScatterThreads) radix_scatter_kernel(
-    const K* __restrict__ kin, K* __restrict__ kout, ColSet cols, uint32_t gen_tid_mask, int64_t n, int shift,
-    int width, int transform, const uint32_t* __restrict__ hist, uint32_t* status, int* tile_counter, int* err) {
-  extern __shared__ __align__(16) unsigned char s_stage_raw[];
-  __shared__ uint32_t s_wcnt[kWarps][kRadixMax];
+__global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint32_t s_tstart[kRadixMax];
-  __shared__ uint32_t s_dbase[kRadixMax];
   __shared__ int64_t s_gdst[kRadixMax];
-  __shared__ uint8_t s_sdig[kTile];
   __shared__ uint32_t s_scan[kWarps];
   __shared__ int s_tile;
+  __shared__ __align__(8) uint64_t s_bar[2];
 
-  const int radix = 1 << width;
+  const int radix = 1 << a.width;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1;
+  K* s_key = (K*)smem;
+  uint16_t* s_inv = (uint16_t*)(smem + a.inv_off);
+  uint8_t* s_sdig = smem + a.sdig_off;
+  uint16_t* s_wcnt = (uint16_t*)(smem + a.wcnt_off);  // [kWarps][kRadixMax]
 
-  if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1);
-  for (int i = threadIdx.x; i < kWarps * kRadixMax; i += kScatterThreads) (&s_wcnt[0][0])[i] = 0;
+  if (threadIdx.x == 0) {
+    s_tile = atomicAdd(a.tile_counter, 1);
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_fence_init();
+  }
   __syncthreads();
   const int tile = s_tile;
-  const int64_t tile_base = (int64_t)tile * kTile;
-  const int tile_n = (int)min64(kTile, n - tile_base);
-  const int64_t seg = tile_base + (int64_t)warp * (32 * kScatterItems);
+  const int64_t tile_base = (int64_t)tile * a.tile_rows;
+  const int tile_n = (int)min64(a.tile_rows, a.n - tile_base);
 
-  // ---- load keys, rank stably within the warp's contiguous segment
-  K key[kScatterItems];
-  uint32_t dig[kScatterItems];
-  uint32_t spos[kScatterItems];
-#pragma unroll
-  for (int i = 0; i < kScatterItems; ++i) {
-    int64_t row = seg + i * 32 + lane;
-    key[i] = row < n ? kin[row] : K(0);
+  // ---- stage the tile: key first (ranking needs only it), then the columns
+  if (a.bulk) {
+    if (threadIdx.x == 0) {
+      uint32_t kb = ((uint32_t)tile_n * sizeof(K)) & ~15u;
+      mbar_expect_tx(&s_bar[0], kb);
+      if (kb) bulk_g2s(s_key, (const K*)a.kin + tile_base, kb, &s_bar[0]);
+      uint32_t cb = 0;
+      for (int c = 0; c < a.cols.n; ++c)
+        if (!((a.gen_mask >> c) & 1u)) cb += ((uint32_t)tile_n * a.cols.size[c]) & ~15u;
+      mbar_expect_tx(&s_bar[1], cb);
+      for (int c = 0; c < a.cols.n; ++c) {
+        if ((a.gen_mask >> c) & 1u) continue;
+        uint32_t b = ((uint32_t)tile_n * a.cols.size[c]) & ~15u;
+        if (b)
+          bulk_g2s(smem + a.col_off[c], (const unsigned char*)a.cols.src[c] + tile_base * a.cols.size[c], b,
+                   &s_bar[1]);
+      }
+    }
+    // the last few elements of a ragged tile with plain loads
+    stage_tail<K>(smem, (const K*)a.kin, tile_base, tile_n, (int)((((uint32_t)tile_n * sizeof(K)) & ~15u) / sizeof(K)));
+    for (int c = 0; c < a.cols.n; ++c) {
+      if ((a.gen_mask >> c) & 1u) continue;
+      const int sz = a.cols.size[c];
+      const int from = (int)((((uint32_t)tile_n * sz) & ~15u) / sz);
+      if (sz == 8)
+        stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, from);
+      else
+        stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, from);
+    }
+  } else {
+    stage_tail<K>(smem, (const K*)a.kin, tile_base, tile_n, 0);
+    for (int c = 0; c < a.cols.n; ++c) {
+      if ((a.gen_mask >> c) & 1u) continue;
+      if (a.cols.size[c] == 8)
+        stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, 0);
+      else
+        stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, 0);
+    }
   }
+  for (int i = threadIdx.x; i < kWarps * kRadixMax; i += kThreads) s_wcnt[i] = 0;
+  if (a.bulk) mbar_wait(&s_bar[0], 0, a.err);
+  __syncthreads();
+
+  // ---- stable rank inside the warp's contiguous rows
+  uint16_t rank[kMaxChunks];
+  uint8_t dg[kMaxChunks];
+  const int seg = warp * a.chunks * 32;
 #pragma unroll
-  for (int i = 0; i < kScatterItems; ++i) {
-    int64_t row = seg + i * 32 + lane;
-    const bool valid = row < n;
-    uint32_t d = valid ? extract_digit<K>(key[i], transform, shift, width) : 0xffffffffu;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
+  for (int i = 0; i < kMaxChunks; ++i) {
+    if (i >= a.chunks) break;
+    const int row = seg + i * 32 + lane;
+    const bool valid = row < tile_n;
+    const uint32_t d = valid ? extract_digit<K>(s_key[row], a.transform, a.shift, a.width) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t cnt = 0;
-    if (valid) cnt = s_wcnt[warp][d];
+    if (valid) cnt = s_wcnt[warp * kRadixMax + d];
     __syncwarp();
-    if (valid && (peers & lt_mask) == 0) s_wcnt[warp][d] = cnt + __popc(peers);
+    if (valid && (peers & lt_mask) == 0) s_wcnt[warp * kRadixMax + d] = (uint16_t)(cnt + __popc(peers));
     __syncwarp();
-    dig[i] = d;
-    spos[i] = cnt + __popc(peers & lt_mask);  // rank among equal digits of this warp so far
+    rank[i] = (uint16_t)(cnt + __popc(peers & lt_mask));
+    dg[i] = (uint8_t)d;
   }
   __syncthreads();
 
-  // ---- per digit: exclusive offsets of the warps, tile count, publish aggregate
-  const int d = threadIdx.x;  // kScatterThreads == kRadixMax
+  // ---- per digit: warp offsets, tile count, publish, global offsets
+  const int d = threadIdx.x;
   uint32_t tcnt = 0;
   if (d < radix) {
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      uint32_t c = s_wcnt[w][d];
-      s_wcnt[w][d] = tcnt;
+      uint32_t c = s_wcnt[w * kRadixMax + d];
+      s_wcnt[w * kRadixMax + d] = (uint16_t)tcnt;
       tcnt += c;
     }
-    st_volatile32(&status[(int64_t)tile * radix + d], (tile == 0 ? kSFlagInc : kSFlagAgg) | tcnt);
+    st_volatile32(&a.status[(int64_t)tile * radix + d], (tile == 0 ? kSFlagInc : kSFlagAgg) | tcnt);
   }
-  uint32_t hv = d < radix ? hist[d] : 0;
-  uint32_t tstart = block_excl_scan256(tcnt, s_scan, nullptr);
-  uint32_t dbase = block_excl_scan256(hv, s_scan, nullptr);
+  const uint32_t hv = d < radix ? a.hist[d] : 0;
+  const uint32_t tstart = block_excl_scan(tcnt, s_scan);
+  const uint32_t dbase = block_excl_scan(hv, s_scan);
   if (d < radix) {
     s_tstart[d] = tstart;
-    s_dbase[d] = dbase;
-    // ---- decoupled look-back over preceding tiles for this digit
     uint32_t excl = 0;
     if (tile > 0) {
       int64_t t = tile - 1;
       uint32_t spins = 0;
       while (t >= 0) {
-        uint32_t w = ld_volatile32(&status[t * radix + d]);
-        uint32_t flag = w & ~kSVal;
+        const uint32_t w = ld_volatile32(&a.status[t * radix + d]);
+        const uint32_t flag = w & ~kSVal;
         if (flag == 0) {
           if (++spins > kSpinLimit) {
-            set_status(err, GJ_ERR_TIMEOUT);
+            set_status(a.err, GJ_ERR_TIMEOUT);
             break;
           }
           continue;
@@ -198,43 +293,45 @@ __global__ void __launch_bounds__(kScatterThreads) radix_scatter_kernel(
         if (flag == kSFlagInc) break;
         --t;
       }
-      st_volatile32(&status[(int64_t)tile * radix + d], kSFlagInc | (excl + tcnt));
+      st_volatile32(&a.status[(int64_t)tile * radix + d], kSFlagInc | (excl + tcnt));
     }
     s_gdst[d] = (int64_t)dbase + excl - tstart;
   }
   __syncthreads();
 
-  // ---- sorted position inside the tile; digit of every sorted position
+  // ---- inverse index: sorted position -> row of the tile
 #pragma unroll
-  for (int i = 0; i < kScatterItems; ++i) {
-    int64_t row = seg + i * 32 + lane;
-    if (row < n) {
-      uint32_t p = s_tstart[dig[i]] + s_wcnt[warp][dig[i]] + spos[i];
-      spos[i] = p;
-      s_sdig[p] = (uint8_t)dig[i];
+  for (int i = 0; i < kMaxChunks; ++i) {
+    if (i >= a.chunks) break;
+    const int row = seg + i * 32 + lane;
+    if (row < tile_n) {
+      const uint32_t p = s_tstart[dg[i]] + s_wcnt[warp * kRadixMax + dg[i]] + rank[i];
+      s_inv[p] = (uint16_t)row;
+      s_sdig[p] = dg[i];
     }
   }
-  // keys
+  __syncthreads();
+
+  // ---- write every column in digit-sorted order
   {
-    K* st = (K*)s_stage_raw;
-#pragma unroll
-    for (int i = 0; i < kScatterItems; ++i) {
-      int64_t row = seg + i * 32 + lane;
-      if (row < n) st[spos[i]] = key[i];
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < tile_n; p += kScatterThreads) kout[s_gdst[s_sdig[p]] + p] = st[p];
-    __syncthreads();
+    K* kout = (K*)a.kout;
+    for (int p = threadIdx.x; p < tile_n; p += kThreads) kout[s_gdst[s_sdig[p]] + p] = s_key[s_inv[p]];
   }
-  // payload columns, all through the same positions
-  for (int c = 0; c < cols.n; ++c) {
-    const bool gen = (gen_tid_mask >> c) & 1u;
-    if (cols.size[c] == 8)
-      scatter_column<int64_t>((const int64_t*)cols.src[c], (int64_t*)cols.dst[c], gen, seg, lane, spos, 0, n,
-                              (int64_t*)s_stage_raw, s_gdst, s_sdig, tile_n, tile_base);
-    else
-      scatter_column<int32_t>((const int32_t*)cols.src[c], (int32_t*)cols.dst[c], gen, seg, lane, spos, 0, n,
-                              (int32_t*)s_stage_raw, s_gdst, s_sdig, tile_n, tile_base);
+  if (a.bulk) mbar_wait(&s_bar[1], 0, a.err);
+  __syncthreads();
+  for (int c = 0; c < a.cols.n; ++c) {
+    const bool gen = (a.gen_mask >> c) & 1u;
+    if (a.cols.size[c] == 8) {
+      const int64_t* st = (const int64_t*)(smem + a.col_off[c]);
+      int64_t* dst = (int64_t*)a.cols.dst[c];
+      for (int p = threadIdx.x; p < tile_n; p += kThreads)
+        dst[s_gdst[s_sdig[p]] + p] = gen ? tile_base + s_inv[p] : st[s_inv[p]];
+    } else {
+      const int32_t* st = (const int32_t*)(smem + a.col_off[c]);
+      int32_t* dst = (int32_t*)a.cols.dst[c];
+      for (int p = threadIdx.x; p < tile_n; p += kThreads)
+        dst[s_gdst[s_sdig[p]] + p] = gen ? (int32_t)(tile_base + s_inv[p]) : st[s_inv[p]];
+    }
   }
 }
 
@@ -250,6 +347,8 @@ __global__ void bounds_kernel(const K* __restrict__ keys, int64_t n, int shift, 
   }
 }
 
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 template <typename K>
 gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* kout, const ColSet& cols_in,
                                 int64_t n, int lo, int hi, int transform, int bits_per_pass) {
@@ -261,12 +360,42 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     pd.shift[q] = plan.shift[q];
     pd.width[q] = plan.width[q];
   }
-  const int64_t tiles = (n + kTile - 1) / kTile;
+  uint32_t gen_mask = 0;
+  int row_bytes = sizeof(K);  // generated tuple ids are staged from the second pass on: count them
+  for (int c = 0; c < cols_in.n; ++c) {
+    if (cols_in.src[c] == nullptr) gen_mask |= 1u << c;
+    row_bytes += cols_in.size[c];
+  }
+  // tile: 512 rows per chunk step; staged bytes + 3 bytes/row of indices within the budget
+  int chunks = kSmemBudget / (kThreads * (row_bytes + 3));
+  chunks = std::max(1, std::min(kMaxChunks, chunks));
+  const int tile_rows = kThreads * chunks;
+  const int64_t tiles = (n + tile_rows - 1) / tile_rows;
+
+  ScatterArgs a{};
+  a.n = n;
+  a.transform = transform;
+  a.tile_rows = tile_rows;
+  a.chunks = chunks;
+  a.gen_mask = gen_mask;
+  int off = tile_rows * (int)sizeof(K);
+  for (int c = 0; c < cols_in.n; ++c) {
+    a.col_off[c] = off;
+    if (!((gen_mask >> c) & 1u)) off += tile_rows * cols_in.size[c];
+  }
+  a.inv_off = off;
+  off += tile_rows * 2;
+  a.sdig_off = off;
+  off += tile_rows;
+  off = (off + 15) & ~15;
+  a.wcnt_off = off;
+  off += kWarps * kRadixMax * 2;
+  const size_t dyn = (size_t)off;
+
   uint32_t* hist = scr.get_as<uint32_t>((size_t)plan.passes * kRadixMax);
-  size_t status_words = (size_t)tiles * kRadixMax;
+  const size_t status_words = (size_t)tiles * kRadixMax;
   uint32_t* status = scr.get_as<uint32_t>(status_words * plan.passes);
   int* counters = scr.get_as<int>(plan.passes);
-  // one scratch buffer (keys + columns) ping-pongs with the output
   K* ktmp = nullptr;
   ColSet tmp = cols_in;
   if (plan.passes > 1) {
@@ -281,39 +410,56 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     return st;
   if ((st = cuda_check(cudaMemsetAsync(counters, 0, sizeof(int) * plan.passes, s))) != GJ_OK) return st;
 
-  int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx.num_sms * 8));
   {
+    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
     LaunchScope ls(ctx, KK_RADIX_HIST);
     radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>(kin, n, pd, transform, hist);
   }
-
-  int max_size = sizeof(K);
-  uint32_t gen_mask = 0;
-  for (int c = 0; c < cols_in.n; ++c) {
-    max_size = std::max(max_size, cols_in.size[c]);
-    if (cols_in.src[c] == nullptr) gen_mask |= 1u << c;
-  }
-  const size_t dyn = (size_t)kTile * max_size;
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTile * 8);
+    cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
     attr_set[sizeof(K) == 8] = true;
   }
   for (int q = 0; q < plan.passes; ++q) {
     const bool to_out = ((plan.passes - 1 - q) % 2) == 0;
-    const K* ki = q == 0 ? kin : (to_out ? ktmp : kout);
-    K* ko = to_out ? kout : ktmp;
-    ColSet cs = cols_in;
+    a.kin = q == 0 ? (const void*)kin : (to_out ? (const void*)ktmp : (const void*)kout);
+    a.kout = to_out ? (void*)kout : (void*)ktmp;
+    a.cols = cols_in;
+    bool bulk = aligned16(a.kin);
     for (int c = 0; c < cols_in.n; ++c) {
       const void* prev_dst = to_out ? tmp.dst[c] : cols_in.dst[c];  // where the previous pass wrote
-      cs.src[c] = q == 0 ? cols_in.src[c] : prev_dst;
-      cs.dst[c] = to_out ? cols_in.dst[c] : tmp.dst[c];
+      a.cols.src[c] = q == 0 ? cols_in.src[c] : prev_dst;
+      a.cols.dst[c] = to_out ? cols_in.dst[c] : tmp.dst[c];
+      if (a.cols.src[c] && !aligned16(a.cols.src[c])) bulk = false;
     }
-    uint32_t gm = q == 0 ? gen_mask : 0u;
+    a.gen_mask = q == 0 ? gen_mask : 0u;
+    a.bulk = bulk ? 1 : 0;
+    a.shift = plan.shift[q];
+    a.width = plan.width[q];
+    a.hist = hist + q * kRadixMax;
+    a.status = status + status_words * q;
+    a.tile_counter = counters + q;
+    a.err = ctx.d_status;
+    if (q > 0 && gen_mask) {
+      // tuple ids now sit in shared memory like any other column
+      int o = tile_rows * (int)sizeof(K);
+      for (int c = 0; c < cols_in.n; ++c) {
+        a.col_off[c] = o;
+        o += tile_rows * cols_in.size[c];
+      }
+      a.inv_off = o;
+      o += tile_rows * 2;
+      a.sdig_off = o;
+      o += tile_rows;
+      o = (o + 15) & ~15;
+      a.wcnt_off = o;
+      o += kWarps * kRadixMax * 2;
+      LaunchScope ls(ctx, KK_RADIX_SCATTER);
+      radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, (size_t)o, s>>>(a);
+      continue;
+    }
     LaunchScope ls(ctx, KK_RADIX_SCATTER);
-    radix_scatter_kernel<K><<<(unsigned)tiles, kScatterThreads, dyn, s>>>(
-        ki, ko, cs, gm, n, plan.shift[q], plan.width[q], transform, hist + q * kRadixMax,
-        status + status_words * q, counters + q, ctx.d_status);
+    radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, dyn, s>>>(a);
   }
   return cuda_check(cudaGetLastError());
 }

@@ -90,6 +90,227 @@ def load():
     return lib
 
 
+BATCH_MAX_AGGS = 8
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("R", Table), ("S", Table), ("group_key", ColRef), ("nagg", ctypes.c_int32),
+                ("ops", ctypes.c_int32 * BATCH_MAX_AGGS), ("agg_cols", ColRef * BATCH_MAX_AGGS),
+                ("out_keys", ctypes.c_void_p), ("out_aggs", ctypes.c_void_p * BATCH_MAX_AGGS),
+                ("capacity", ctypes.c_int64), ("d_ngroups", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("build_rows", ctypes.c_int32), ("probe_rows", ctypes.c_int32), ("lookahead", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+def _load_batch(lib):
+    if getattr(lib, "_batch_ready", False):
+        return
+    P = ctypes.POINTER
+    lib.gj_batch_create.argtypes = [P(Query), ctypes.c_int32, P(BatchConfig), P(ctypes.c_void_p), ctypes.c_void_p]
+    lib.gj_batch_create.restype = ctypes.c_int32
+    lib.gj_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.gj_batch_launch.restype = ctypes.c_int32
+    lib.gj_batch_get_config.argtypes = [ctypes.c_void_p, P(BatchConfig)]
+    lib.gj_batch_get_config.restype = ctypes.c_int32
+    lib.gj_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.gj_batch_destroy.restype = ctypes.c_int32
+    lib._batch_ready = True
+
+
+class BatchPlan:
+    """Many join -> group-by queries run as one persistent launch (gj_batch_*).
+
+    Each query is (rkey, rcols, skey, scols, group_key, aggs, agg_cols) with the
+    conventions of join_groupby; outputs are allocated here and kept alive."""
+
+    def __init__(self, queries, config=None):
+        lib = load()
+        _load_batch(lib)
+        self._keep = []
+        arr = (Query * max(1, len(queries)))()
+        self.outputs = []
+        for i, (rkey, rcols, skey, scols, gk, aggs, agg_cols) in enumerate(queries):
+            q = arr[i]
+            q.R = make_table(rkey, rcols)
+            q.S = make_table(skey, scols)
+            q.group_key = ColRef(*[int(x) for x in gk])
+            q.nagg = len(aggs)
+            for j, (a, ref) in enumerate(zip(aggs, agg_cols)):
+                q.ops[j] = AGG[a] if isinstance(a, str) else int(a)
+                q.agg_cols[j] = ColRef(*[int(x) for x in ref])
+            cap = max(1, 2 * int(gk[2]) - 1)
+            okeys = torch.empty(cap, dtype=torch.int64, device=rkey.device)
+            oaggs = [torch.empty(cap, dtype=torch.int64, device=rkey.device) for _ in aggs]
+            ng = torch.zeros(1, dtype=torch.int64, device=rkey.device)
+            q.out_keys = okeys.data_ptr()
+            for j, t in enumerate(oaggs):
+                q.out_aggs[j] = t.data_ptr()
+            q.capacity = cap
+            q.d_ngroups = ng.data_ptr()
+            self.outputs.append((okeys, oaggs, ng))
+            self._keep.append((rkey, rcols, skey, scols))
+        cfg = BatchConfig(*(config or (0, 0, 0, 0)))
+        plan = ctypes.c_void_p()
+        _raise(lib.gj_batch_create(arr, len(queries), ctypes.byref(cfg), ctypes.byref(plan), _stream()),
+               "gj_batch_create")
+        self._plan = plan
+        self._lib = lib
+
+    def launch(self):
+        _raise(self._lib.gj_batch_launch(self._plan, _stream()), "gj_batch_launch")
+
+    def config(self):
+        c = BatchConfig()
+        _raise(self._lib.gj_batch_get_config(self._plan, ctypes.byref(c)), "gj_batch_get_config")
+        return (c.build_rows, c.probe_rows, c.lookahead, c.blocks_per_sm)
+
+    def results(self):
+        """[(keys, [aggs], g)] on the host after synchronising."""
+        torch.cuda.synchronize()
+        out = []
+        for okeys, oaggs, ng in self.outputs:
+            g = int(ng.item())
+            out.append((okeys[:g].cpu().numpy(), [a[:g].cpu().numpy() for a in oaggs], g))
+        return out
+
+    def close(self):
+        if self._plan:
+            self._lib.gj_batch_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 12, 64, 6, 5382
+
+
+def _load_mlp(lib):
+    if getattr(lib, "_mlp_ready", False):
+        return
+    p, i32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
+    P = ctypes.POINTER
+    lib.gj_mlp_forward.argtypes = [p, p, i32, p, p]
+    lib.gj_mlp_loss_grad.argtypes = [p, p, p, p, i32, p, p, p]
+    lib.gj_mlp_adam_step.argtypes = [p, p, p, p, i32, f32, f32, f32, f32, p]
+    lib.gj_mlp_sgd_step.argtypes = [p, p, f32, p]
+    lib.gj_mlp_select.argtypes = [p, p, i32, p, p, p]
+    lib.gj_selector_set.argtypes = [p, p, p]
+    lib.gj_query_features.argtypes = [P(Table), P(Table), i32, P(Options), p]
+    lib.gj_heuristic_choose.argtypes = [P(Table), P(Table), i32, P(Options), P(i32), P(i32)]
+    for f in ("gj_mlp_forward", "gj_mlp_loss_grad", "gj_mlp_adam_step", "gj_mlp_sgd_step", "gj_mlp_select",
+              "gj_selector_set", "gj_query_features", "gj_heuristic_choose"):
+        getattr(lib, f).restype = i32
+    lib._mlp_ready = True
+
+
+def _f32(t: torch.Tensor):
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(theta: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+    """y[b][6] of the selector network for device features x[b][12]."""
+    lib = load()
+    _load_mlp(lib)
+    y = torch.empty((x.shape[0], MLP_OUT), dtype=torch.float32, device=x.device)
+    _raise(lib.gj_mlp_forward(_f32(theta), _f32(x), x.shape[0], _f32(y), _stream()), "gj_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(theta, x, t, mask):
+    """(loss tensor[1], grad tensor[MLP_PARAMS]) of the masked squared error."""
+    lib = load()
+    _load_mlp(lib)
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    _raise(lib.gj_mlp_loss_grad(_f32(theta), _f32(x), _f32(t), _f32(mask), x.shape[0], _f32(grad), _f32(loss),
+                                _stream()), "gj_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    lib = load()
+    _load_mlp(lib)
+    _raise(lib.gj_mlp_adam_step(_f32(theta), _f32(grad), _f32(m), _f32(v), step, lr, beta1, beta2, eps, _stream()),
+           "gj_mlp_adam_step")
+
+
+def mlp_sgd_step(theta, grad, lr):
+    lib = load()
+    _load_mlp(lib)
+    _raise(lib.gj_mlp_sgd_step(_f32(theta), _f32(grad), lr, _stream()), "gj_mlp_sgd_step")
+
+
+def mlp_select(theta, x):
+    """(join variant codes, group-by variant codes) chosen by the network for each feature row."""
+    lib = load()
+    _load_mlp(lib)
+    n = x.shape[0]
+    jv = torch.empty(n, dtype=torch.int32, device=x.device)
+    gv = torch.empty(n, dtype=torch.int32, device=x.device)
+    _raise(lib.gj_mlp_select(_f32(theta), _f32(x), n, ctypes.c_void_p(jv.data_ptr()), ctypes.c_void_p(gv.data_ptr()),
+                             _stream()), "gj_mlp_select")
+    return jv, gv
+
+
+def selector_set(theta_host, mean, std):
+    """Install (or with theta_host None, remove) the network used by AUTO + selector=1."""
+    import numpy as np
+    lib = load()
+    _load_mlp(lib)
+    if theta_host is None:
+        _raise(lib.gj_selector_set(None, None, None), "gj_selector_set")
+        return
+    th = np.ascontiguousarray(theta_host, dtype=np.float32)
+    mu = np.ascontiguousarray(mean, dtype=np.float32)
+    sd = np.ascontiguousarray(std, dtype=np.float32)
+    _raise(lib.gj_selector_set(th.ctypes.data, mu.ctypes.data, sd.ctypes.data), "gj_selector_set")
+
+
+def _shape_table(n: int, key_bytes: int, ncols: int, col_bytes: int = 4) -> Table:
+    t = Table()
+    t.key_type = I64 if key_bytes == 8 else I32
+    t.ncols = ncols
+    t.n = n
+    for c in range(ncols):
+        t.col_type[c] = I64 if col_bytes == 8 else I32
+    return t
+
+
+def query_features(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups):
+    """The 12 raw selector features of a query shape (gj_query_features)."""
+    import numpy as np
+    lib = load()
+    _load_mlp(lib)
+    R = _shape_table(nr, key_bytes, ncols_r)
+    S = _shape_table(ns, key_bytes, ncols_s)
+    o = options(zipf_hint=zipf, match_ratio_hint=mr, groups_hint=int(groups))
+    out = np.zeros(MLP_IN, dtype=np.float32)
+    _raise(lib.gj_query_features(ctypes.byref(R), ctypes.byref(S), nagg, ctypes.byref(o), out.ctypes.data),
+           "gj_query_features")
+    return out
+
+
+def heuristic_choose(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups):
+    """(join variant, group-by variant) under the paper's rules (gj_heuristic_choose)."""
+    lib = load()
+    _load_mlp(lib)
+    R = _shape_table(nr, key_bytes, ncols_r)
+    S = _shape_table(ns, key_bytes, ncols_s)
+    o = options(zipf_hint=zipf, match_ratio_hint=mr, groups_hint=int(groups))
+    jv, gv = ctypes.c_int32(), ctypes.c_int32()
+    _raise(lib.gj_heuristic_choose(ctypes.byref(R), ctypes.byref(S), nagg, ctypes.byref(o), ctypes.byref(jv),
+                                   ctypes.byref(gv)), "gj_heuristic_choose")
+    return jv.value, gv.value
+
+
 def profile_enable(on: bool):
     """Record CUDA events around every library kernel launch on its stream."""
     load().gj_profile_enable(1 if on else 0)
@@ -194,7 +415,7 @@ def radix_partition(key: torch.Tensor, cols, bit_lo: int, bit_hi: int, transform
 
 def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | None = None,
          radix_bits: int = 0, bits_per_pass: int = 0, sync: bool = True, out=None, count=None,
-         match_ratio_hint: float = -1.0, zipf_hint: float = -1.0):
+         match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, selector: int = 0):
     """R join S on key (Sec. 2.2). Returns (T.key, [T.cols: R's then S's], device count tensor).
 
     ``out`` may pass preallocated (key, cols) outputs and ``count`` a device int64[1]."""
@@ -219,7 +440,7 @@ def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | N
     if count is None:
         count = torch.zeros(1, dtype=torch.int64, device=rkey.device)
     o = options(join=variant, radix_bits=radix_bits, bits_per_pass=bits_per_pass, sync=sync,
-                match_ratio_hint=match_ratio_hint, zipf_hint=zipf_hint)
+                match_ratio_hint=match_ratio_hint, zipf_hint=zipf_hint, selector=selector)
     _raise(lib.gj_join(ctypes.byref(R), ctypes.byref(S), ctypes.byref(o), ctypes.byref(T), capacity,
                        ctypes.c_void_p(count.data_ptr()), _stream()), "gj_join")
     return tkey, tcols, count

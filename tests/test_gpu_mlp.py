@@ -1,0 +1,123 @@
+"""Selector network kernels vs the float64 reference (oracle.mlp), and what the
+trained network gains over the paper's rules on held-out timed queries."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+
+def _data(b, seed):
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(0, 0.3, ref.N_PARAMS)
+    x = rng.normal(0, 1, (b, ref.D_IN))
+    t = rng.normal(0, 1, (b, ref.D_OUT))
+    mask = (rng.random((b, ref.D_OUT)) < 0.8).astype(np.float64)
+    return theta, x, t, mask
+
+
+dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("b", [1, 7, 32, 33, 500])
+def test_forward_matches_reference(gj, b):
+    theta, x, _, _ = _data(b, b)
+    y = gj.mlp_forward(dev(theta), dev(x)).cpu().numpy()
+    want, _ = ref.forward(theta, x)
+    assert np.allclose(y, want, rtol=1e-4, atol=1e-4)
+
+
+@pytest.mark.parametrize("b", [1, 31, 64, 257])
+def test_loss_and_gradient_match_reference(gj, b):
+    theta, x, t, mask = _data(b, 100 + b)
+    loss, grad = gj.mlp_loss_grad(dev(theta), dev(x), dev(t), dev(mask))
+    want_loss, want_grad = ref.grad(theta, x, t, mask)
+    assert float(loss.item()) == pytest.approx(want_loss, rel=1e-4)
+    g = grad.cpu().numpy()
+    scale = np.abs(want_grad).max()
+    assert np.max(np.abs(g - want_grad)) <= 1e-4 * scale
+    # the two-level reduction is deterministic
+    loss2, grad2 = gj.mlp_loss_grad(dev(theta), dev(x), dev(t), dev(mask))
+    assert torch.equal(grad, grad2) and torch.equal(loss, loss2)
+
+
+def test_adam_and_sgd_steps_match_reference(gj):
+    rng = np.random.default_rng(3)
+    theta = rng.normal(0, 0.3, ref.N_PARAMS)
+    g1 = rng.normal(0, 1, ref.N_PARAMS)
+    g2 = rng.normal(0, 1, ref.N_PARAMS)
+    th = dev(theta)
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    want, mm, vv = theta, np.zeros_like(theta), np.zeros_like(theta)
+    for step, g in ((1, g1), (2, g2)):
+        gj.mlp_adam_step(th, dev(g), m, v, step, lr=1e-2)
+        want, mm, vv = ref.adam_step(want, g, mm, vv, step, 1e-2)
+    assert np.allclose(th.cpu().numpy(), want, rtol=1e-4, atol=1e-6)
+    th2 = dev(theta)
+    gj.mlp_sgd_step(th2, dev(g1), 0.5)
+    assert np.allclose(th2.cpu().numpy(), ref.sgd_step(theta, g1, 0.5), rtol=1e-5, atol=1e-6)
+
+
+def test_select_is_argmin_per_family(gj):
+    theta, x, _, _ = _data(300, 9)
+    jv, gv = gj.mlp_select(dev(theta), dev(x))
+    y, _ = ref.forward(theta, x)
+    assert np.array_equal(jv.cpu().numpy(), 1 + np.argmin(y[:, :3], 1))
+    assert np.array_equal(gv.cpu().numpy(), 1 + np.argmin(y[:, 3:], 1))
+
+
+def test_training_fits_a_known_function(gj):
+    from paper_2312_00720_gb300 import selector
+    rng = np.random.default_rng(0)
+    recs = []
+    for i in range(400):
+        f = rng.normal(0, 1, 12)
+        ms = {v: float(np.exp(0.5 * f[k] - 0.3 * f[(k + 3) % 12])) for k, v in enumerate(selector.ALL_VARIANTS)}
+        recs.append({"features": f.tolist(), "ms": ms})
+    theta, mean, std, losses = selector.train(recs, steps=1500, lr=3e-3)
+    assert losses[-1] < 0.05 * losses[0]
+
+
+def test_selector_drives_auto(gj):
+    """With a network whose output prefers NPHJ and PGB, AUTO + selector=MLP runs them."""
+    from paper_2312_00720_gb300 import workloads as wl
+    import oracle
+    th = np.zeros(ref.N_PARAMS, dtype=np.float32)
+    p = ref.unpack(th.astype(np.float64))
+    b3 = np.array([1.0, 1.0, -1.0, 1.0, 1.0, -1.0])   # y = b3: argmins NPHJ, PGB
+    th = ref.pack({**p, "b3": b3}).astype(np.float32)
+    gj.selector_set(th, np.zeros(12), np.ones(12))
+    try:
+        w = wl.join_workload(2000, 8000, 1, 1, seed=1)
+        d = lambda a: torch.from_numpy(a).cuda()
+        gj.profile_read()
+        gj.profile_enable(True)
+        tk, tc, cnt = gj.join(d(w["rkey"]), [d(w["rcols"][0])], d(w["skey"]), [d(w["scols"][0])], variant="auto",
+                              selector=1)
+        prof = gj.profile_read()
+        gj.profile_enable(False)
+        assert "nphj_probe" in prof and "phj_probe" not in prof
+        m = int(cnt.item())
+        got = np.stack([tk[:m].cpu().numpy(), tc[0][:m].cpu().numpy(), tc[1][:m].cpu().numpy()], 1)
+        want = oracle.join(w["rkey"], w["rcols"], w["skey"], w["scols"])
+        assert np.array_equal(oracle.canonical(got.astype(np.int64)), oracle.canonical(want))
+    finally:
+        gj.selector_set(None, None, None)
+
+
+@pytest.mark.slow
+def test_trained_selector_beats_the_paper_rules_on_held_out_queries(gj, tmp_path):
+    """Time every variant on a seeded grid (reduced sizes), train on 80 %, and
+    compare regrets on the held-out 20 %."""
+    from paper_2312_00720_gb300 import selector
+    pts = selector.grid(200, seed=7, log_s=(14.0, 20.0))
+    recs = selector.sweep(str(tmp_path / "timings.jsonl"), pts, reps=3)
+    train, held = selector.split(recs, 0.8, seed=1)
+    theta, mean, std, losses = selector.train(train, steps=3000)
+    ev = selector.evaluate(held, theta, mean, std)
+    print(ev)
+    assert losses[-1] < losses[0]
+    assert ev["mlp_mean_regret"] <= ev["heuristic_mean_regret"]
