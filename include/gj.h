@@ -134,6 +134,30 @@ gj_status gj_get_device_status(void* stream);
 gj_status gj_radix_partition(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
                              gj_table* out, int64_t* d_offsets, const gj_options* opt, void* stream);
 
+/* radix-partition without any device allocation. For callers that must not
+ * allocate device memory: code that runs while another component owns the
+ * device's memory budget (a framework that reserved it all in its own pool),
+ * code called from inside an allocator or a memory-pressure handler, and
+ * latency-bound paths that cannot afford the implicit device synchronisation
+ * and pool growth that cudaMalloc/cudaFree can cause. Every other entry point
+ * takes scratch from cudaMallocAsync or the gj_set_allocator hook; this one
+ * takes it from a fixed array inside the library. The paper has no counterpart:
+ * the result is exactly gj_radix_partition's for one pass.
+ * Limits: bit_hi - bit_lo <= 8 (a single pass) and in->n <= 2^21 rows, else
+ * GJ_ERR_UNSUPPORTED; arguments as for gj_radix_partition otherwise.
+ * Memory: the array is about 4 MB and is resident on every device that loads
+ * the library until the process exits. The call makes no cudaMalloc, cudaFree
+ * or allocator-hook call. Its first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture. All calls share the one array, which keeps what the last call
+ * left in it (each call clears the part it uses): calls whose work can overlap
+ * on the GPU -- unordered streams or concurrent host threads -- race on it, so
+ * the caller must order them. sync = 1 synchronises `stream` and returns the
+ * errors its kernels recorded; with sync = 0 they are kept for the next sync = 1
+ * call of this entry point. */
+gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
+                                     gj_table* out, int64_t* d_offsets, int32_t sync, void* stream);
+
 /* Inner equi-join (Sec. 2.2): T(key, R.cols.., S.cols..) = { (r.key, r.., s..) :
  * r in R, s in S, r.key = s.key }. R.key must be unique (a primary key); a
  * repeated key yields GJ_ERR_DUPLICATE_KEY. R and S keys have the same type.

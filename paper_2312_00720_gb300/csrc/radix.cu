@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "gj_internal.cuh"
 
@@ -496,6 +497,98 @@ gj_status radix_partition_run(const Ctx& ctx, Scratch& scr, int key_type, const 
                                         bits_per_pass);
 }
 
+// ---------------------------------------------------------------- allocation-free variant
+// For callers that cannot allocate device memory: a single-pass partition whose
+// scratch (digit histogram, tile counter, look-back words) is this file-scope
+// array instead of stream-ordered allocations. It holds kNoAllocWords 32-bit
+// words (about 4 MB) on every device that loads the library, until exit.
+namespace {
+constexpr int64_t kNoAllocMaxRows = int64_t(1) << 21;
+constexpr int kNoAllocMaxTiles = (int)(kNoAllocMaxRows / kThreads);  // tiles hold >= 512 rows
+constexpr size_t kNoAllocHead = 320;                                  // histogram (256) + counter, padded
+constexpr size_t kNoAllocWords = kNoAllocHead + (size_t)kNoAllocMaxTiles * kRadixMax;
+__device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+__device__ __align__(256) int g_noalloc_status[64];
+constexpr int kNoAllocDevices = 64;
+uint32_t* g_noalloc_ptr[kNoAllocDevices] = {nullptr};
+int* g_noalloc_err[kNoAllocDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+template <typename K>
+gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* in, gj_table* out, int lo, int hi,
+                            int transform, int64_t* d_off) {
+  const int64_t n = in->n;
+  const int width = hi - lo;
+  ColSet cols{};
+  cols.n = in->ncols;
+  int row_bytes = sizeof(K);
+  for (int c = 0; c < in->ncols; ++c) {
+    cols.src[c] = in->cols[c];
+    cols.dst[c] = out->cols[c];
+    cols.size[c] = dtype_size(in->col_type[c]);
+    row_bytes += cols.size[c];
+  }
+  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * (row_bytes + 3))));
+  const int tile_rows = kThreads * chunks;
+  const int64_t tiles = (n + tile_rows - 1) / tile_rows;
+  ScatterArgs a{};
+  a.kin = in->key;
+  a.kout = out->key;
+  a.cols = cols;
+  a.n = n;
+  a.shift = lo;
+  a.width = width;
+  a.transform = transform;
+  a.hist = scratch;
+  a.tile_counter = (int*)(scratch + 256);
+  a.status = scratch + kNoAllocHead;
+  a.err = ctx.d_status;
+  a.tile_rows = tile_rows;
+  a.chunks = chunks;
+  bool bulk = aligned16(in->key);
+  for (int c = 0; c < cols.n; ++c)
+    if (!aligned16(cols.src[c])) bulk = false;
+  a.bulk = bulk ? 1 : 0;
+  int off = tile_rows * (int)sizeof(K);
+  for (int c = 0; c < cols.n; ++c) {
+    a.col_off[c] = off;
+    off += tile_rows * cols.size[c];
+  }
+  a.inv_off = off;
+  off += tile_rows * 2;
+  a.sdig_off = off;
+  off += tile_rows;
+  off = (off + 15) & ~15;
+  a.wcnt_off = off;
+  off += kWarps * kRadixMax * 2;
+  cudaStream_t s = ctx.stream;
+  gj_status st;
+  // the array keeps the previous call's contents: clear what must start at zero
+  if ((st = cuda_check(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * (kNoAllocHead + (size_t)tiles * kRadixMax), s))) !=
+      GJ_OK)
+    return st;
+  PassDigits pd{};
+  pd.passes = 1;
+  pd.shift[0] = lo;
+  pd.width[0] = width;
+  {
+    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
+    LaunchScope ls(ctx, KK_RADIX_HIST);
+    radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>((const K*)in->key, n, pd, transform, scratch);
+  }
+  if ((st = cuda_check(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBudget + 16 * 1024))) != GJ_OK)
+    return st;
+  {
+    LaunchScope ls(ctx, KK_RADIX_SCATTER);
+    radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, (size_t)off, s>>>(a);
+  }
+  if ((st = cuda_check(cudaGetLastError())) != GJ_OK) return st;
+  if (d_off) return partition_bounds_run(ctx, in->key_type, out->key, n, lo, width, transform, d_off);
+  return GJ_OK;
+}
+}  // namespace
+
 gj_status partition_bounds_run(const Ctx& ctx, int key_type, const void* keys, int64_t n, int lo, int width,
                                int transform, int64_t* d_off) {
   int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 256) / 256, (int64_t)ctx.num_sms * 8));
@@ -508,3 +601,62 @@ gj_status partition_bounds_run(const Ctx& ctx, int key_type, const void* keys, i
 }
 
 }  // namespace gj
+
+extern "C" gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_lo, int32_t bit_hi,
+                                                int32_t key_transform, gj_table* out, int64_t* d_offsets,
+                                                int32_t sync, void* stream) {
+  using namespace gj;
+  if (!in || !out) return GJ_ERR_INVALID_ARG;
+  for (const gj_table* t : {in, (const gj_table*)out}) {
+    if ((t->key_type != GJ_I32 && t->key_type != GJ_I64) || t->ncols < 0 || t->ncols > GJ_MAX_COLS || t->n < 0)
+      return GJ_ERR_INVALID_ARG;
+    if (in->n > 0 && !t->key) return GJ_ERR_INVALID_ARG;
+    for (int c = 0; c < t->ncols; ++c)
+      if ((t->col_type[c] != GJ_I32 && t->col_type[c] != GJ_I64) || (in->n > 0 && !t->cols[c]))
+        return GJ_ERR_INVALID_ARG;
+  }
+  if (out->key_type != in->key_type || out->ncols != in->ncols || out->n < in->n) return GJ_ERR_INVALID_ARG;
+  for (int c = 0; c < in->ncols; ++c)
+    if (out->col_type[c] != in->col_type[c]) return GJ_ERR_INVALID_ARG;
+  const int kbits = in->key_type == GJ_I64 ? 64 : 32;
+  if (bit_lo < 0 || bit_hi <= bit_lo || bit_hi > kbits || key_transform < 0 || key_transform > 2)
+    return GJ_ERR_INVALID_ARG;
+  // beyond the fixed scratch: one pass of at most 8 bits over at most 2^21 rows
+  if (bit_hi - bit_lo > 8 || in->n > kNoAllocMaxRows) return GJ_ERR_UNSUPPORTED;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocDevices) return GJ_ERR_CUDA;
+  Ctx ctx{};
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // one-time set-up on this device: the device addresses of the arrays
+      void* p = nullptr;
+      void* e = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return GJ_ERR_CUDA;
+      if (cudaGetSymbolAddress(&e, g_noalloc_status) != cudaSuccess) return GJ_ERR_CUDA;
+      g_noalloc_ptr[dev] = (uint32_t*)p;
+      g_noalloc_err[dev] = (int*)e;
+    }
+    ctx.d_status = g_noalloc_err[dev];
+  }
+  ctx.stream = (cudaStream_t)stream;
+  ctx.device = dev;
+  cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&ctx.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (in->n == 0) {
+    if (d_offsets) return partition_bounds_run(ctx, in->key_type, out->key, 0, bit_lo, bit_hi - bit_lo, key_transform,
+                                               d_offsets);
+    return GJ_OK;
+  }
+  gj_status st = in->key_type == GJ_I64
+                     ? noalloc_partition<int64_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform,
+                                                  d_offsets)
+                     : noalloc_partition<int32_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform,
+                                                  d_offsets);
+  if (st != GJ_OK || !sync) return st;
+  int h = 0;
+  if (cudaStreamSynchronize(ctx.stream) != cudaSuccess) return GJ_ERR_CUDA;
+  if (cudaMemcpy(&h, ctx.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GJ_ERR_CUDA;
+  if (h != 0 && cudaMemset(ctx.d_status, 0, sizeof(int)) != cudaSuccess) return GJ_ERR_CUDA;
+  return (gj_status)h;
+}

@@ -413,6 +413,30 @@ def radix_partition(key: torch.Tensor, cols, bit_lo: int, bit_hi: int, transform
     return kout_t, cols_out, off
 
 
+def radix_partition_noalloc(key: torch.Tensor, cols, bit_lo: int, bit_hi: int, transform: int = 0,
+                            offsets: bool = False, sync: bool = True, out=None):
+    """radix_partition for one pass of at most 8 bits, through the entry point that
+    allocates no device memory (its scratch is a fixed array in the library).
+    ``out`` may pass preallocated (key, [cols]) outputs."""
+    lib = load()
+    if not getattr(lib, "_noalloc_ready", False):
+        P = ctypes.POINTER
+        lib.gj_radix_partition_noalloc.argtypes = [P(Table), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(Table),
+                                                   ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+        lib.gj_radix_partition_noalloc.restype = ctypes.c_int32
+        lib._noalloc_ready = True
+    cols = list(cols)
+    kin = make_table(key, cols)
+    if out is None:
+        out = (torch.empty_like(key), [torch.empty_like(c) for c in cols])
+    kout = make_table(out[0], out[1])
+    off = torch.empty((1 << (bit_hi - bit_lo)) + 1, dtype=torch.int64, device=key.device) if offsets else None
+    _raise(lib.gj_radix_partition_noalloc(ctypes.byref(kin), bit_lo, bit_hi, transform, ctypes.byref(kout),
+                                          None if off is None else off.data_ptr(), 1 if sync else 0, _stream()),
+           "gj_radix_partition_noalloc")
+    return out[0], out[1], off
+
+
 def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | None = None,
          radix_bits: int = 0, bits_per_pass: int = 0, sync: bool = True, out=None, count=None,
          match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, selector: int = 0):
