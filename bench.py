@@ -120,6 +120,92 @@ def cpu_baseline(sample_shift: int = 2):
                       f"{dt:.1f} s"}
 
 
+def _event_ms(fn, steps: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20):
+    """Plain grouped aggregation: 2^27 rows, int32 keys from 2^log2_groups ids,
+    3 int32 value columns, COUNT + SUM/MIN/MAX per column (10 int64 aggregates)."""
+    import torch
+    n, g = 1 << 27, 1 << log2_groups
+    w = wl.groupby_workload(n, g, nvals=3, seed=77)
+    key = torch.from_numpy(w["key"]).cuda()
+    vals = [torch.from_numpy(v).cuda() for v in w["vals"]]
+    aggs = ["count"] + ["sum", "min", "max"] * 3
+    cols = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
+    distinct = int(np.unique(w["key"]).size)
+    min_bytes = n * (4 + 12) + distinct * (4 + 80)
+    out = {"workload": f"n=2^27 int32 keys over 2^{log2_groups} ids ({distinct} groups), 3 int32 values, "
+                       f"COUNT+SUM/MIN/MAX per column", "min_bytes": min_bytes}
+    for v in ("hgb", "sgb", "pgb"):
+        okeys, outs, ng = gj.groupby(key, vals, aggs, cols, variant=v, sync=True)
+        assert int(ng.item()) == distinct
+        ms = _event_ms(lambda: gj.groupby(key, vals, aggs, cols, variant=v, sync=False), steps)
+        out[v] = {"ms": ms, "gtuples_s": n / (ms * 1e-3) / 1e9,
+                  "min_bytes_frac": min_bytes / (ms * 1e-3) / 1e9 / peak}
+    del key, vals
+    return out
+
+
+def bench_one_query(gj, wl, steps: int = 20):
+    """One query: |R| = 2^20 ⋈ |S| = 2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay), not materialised."""
+    import torch
+    w = wl.join_groupby_workload()
+    d = lambda a: torch.from_numpy(a).cuda()
+    rk, rc, sk, sc = d(w["rkey"]), [d(w["rcols"][0])], d(w["skey"]), [d(w["scols"][0])]
+    out = {"workload": "|R|=2^20, |S|=2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay); inputs 40 MB (L2-resident)"}
+    for v in ("nphj", "phj_tr"):
+        args = (rk, rc, sk, sc, (0, 0, 1024), ["sum", "count"], [(1, 0, 0), (1, 0, 0)])
+        okeys, outs, ng = gj.join_groupby(*args, variant=v, sync=True)
+        assert int(outs[1][: int(ng.item())].sum().item()) == 1 << 22
+        ms = _event_ms(lambda: gj.join_groupby(*args, variant=v, sync=False), steps)
+        out[v] = {"us": ms * 1e3, "gtuples_s": ((1 << 20) + (1 << 22)) / (ms * 1e-3) / 1e9}
+    return out
+
+
+def bench_batch(gj, wl, steps: int = 5):
+    """512 join + group-by instances: one persistent graph launch vs 512 sequential gj_join_groupby calls."""
+    import torch
+    ws = wl.batch_workload(512, seed=7)
+    d = lambda a: torch.from_numpy(a).cuda()
+    aggs = ["count", "sum", "sum", "sum"]
+    refs = [(1, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)]
+    qs = [(d(w["rkey"]), [d(c) for c in w["rcols"]], d(w["skey"]), [d(c) for c in w["scols"]],
+           (0, 0, w["modulus"]), aggs, refs) for w in ws]
+    t0 = time.perf_counter()
+    plan = gj.BatchPlan(qs)
+    tune_s = time.perf_counter() - t0
+    batched = _event_ms(plan.launch, steps)
+    res = plan.results()
+    assert gj.device_status() == 0
+    assert all(int(r[1][0].sum()) == len(w["skey"]) for r, w in zip(res, ws))
+
+    def sequential():
+        for q in qs:
+            gj.join_groupby(*q, variant="auto", sync=False, capacity=2 * q[4][2] - 1)
+
+    seq = _event_ms(sequential, max(1, steps // 2))
+    rows = sum(len(w["rkey"]) + len(w["skey"]) for w in ws)
+    cfg = plan.config()
+    plan.close()
+    return {"workload": "512 instances, |R| log-uniform [2^10, 2^20], |S| = 4|R|, 2 int32 payloads per side, "
+                        "GROUP BY R.p0 mod G (G log-uniform [2^2, 2^16]), COUNT, SUM(S.p0), SUM(S.p1), SUM(R.p1)",
+            "rows": rows, "batched_ms": batched, "sequential_ms": seq, "speedup": seq / batched,
+            "batched_gtuples_s": rows / (batched * 1e-3) / 1e9, "sequential_gtuples_s": rows / (seq * 1e-3) / 1e9,
+            "tuned_config": {"build_rows": cfg[0], "probe_rows": cfg[1], "lookahead": cfg[2], "blocks_per_sm": cfg[3]},
+            "tune_and_capture_s": tune_s}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -170,6 +256,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="phj_tr", choices=["phj_tr", "phj_ur", "nphj"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the group-by, one-query and batched lines")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--scale", type=int, default=0, help="divide |R| and |S| by 2^scale (profiling captures only)")
     args = ap.parse_args()
@@ -314,6 +401,12 @@ def main():
         }
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline()
+        if not args.no_extras and world == 1:
+            # the other hot-path rows, measured live on the same GPU
+            del h_in, h_out
+            out["groupby"] = bench_groupby(gj, wl, peak)
+            out["one_query"] = bench_one_query(gj, wl)
+            out["batched"] = bench_batch(gj, wl)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

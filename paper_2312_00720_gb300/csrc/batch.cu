@@ -217,15 +217,23 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(const BInst* __restric
       }
       if (lane == 31) s_scan[warp] = x;
       __syncthreads();
-      if (t == 0) {
+      if (warp == 0) {
         uint32_t run = 0;
-        for (int w = 0; w < kBThreads / 32; ++w) {
-          uint32_t cc = s_scan[w];
-          s_scan[w] = run;
-          run += cc;
+        for (int w = 0; w < kBThreads / 32; ++w) run += s_scan[w];
+        __syncwarp();
+        if (lane == 0) {
+          uint32_t r = 0;
+          for (int w = 0; w < kBThreads / 32; ++w) {
+            const uint32_t cc = s_scan[w];
+            s_scan[w] = r;
+            r += cc;
+          }
         }
-        s_base = lookback_scan((uint64_t*)(c + 4), T.idx, run, err);
-        if (T.idx == I.nemit - 1) *I.d_ngroups = (int64_t)(s_base + run);
+        const uint64_t excl = lookback_scan_warp((uint64_t*)(c + 4), T.idx, run, err);
+        if (lane == 0) {
+          s_base = excl;
+          if (T.idx == I.nemit - 1) *I.d_ngroups = (int64_t)(excl + run);
+        }
       }
       __syncthreads();
       int64_t o = (int64_t)s_base + s_scan[warp] + x - cnt;

@@ -120,6 +120,93 @@ __device__ __forceinline__ uint64_t lookback_scan(uint64_t* st, int64_t tile, ui
   return excl;
 }
 
+// Warp-wide look-back: called by all 32 lanes of one warp of tile `tile`. Lanes
+// read 32 predecessors per round trip (lane l reads tile base - l), so a chain
+// of n aggregate-only predecessors costs n / 32 round trips instead of n.
+// Returns the exclusive prefix in every lane and publishes the inclusive value.
+__device__ __forceinline__ uint64_t lookback_scan_warp(uint64_t* st, int64_t tile, uint64_t agg, int* status) {
+  const int lane = threadIdx.x & 31;
+  if (tile == 0) {
+    if (lane == 0) st_volatile(&st[0], kFlagInc | agg);
+    __syncwarp();
+    return 0;
+  }
+  if (lane == 0) st_volatile(&st[tile], kFlagAgg | agg);
+  uint64_t excl = 0;
+  int64_t base = tile - 1;
+  uint32_t spins = 0;
+  bool timed_out = false;
+  while (base >= 0) {
+    const int64_t idx = base - lane;
+    uint64_t w = idx >= 0 ? ld_volatile(&st[idx]) : kFlagInc;
+    // every predecessor was taken by a running block: wait until all 32 have a flag
+    while (__any_sync(0xffffffffu, (w & ~kValMask) == 0)) {
+      if (++spins > kSpinLimit) {
+        timed_out = true;
+        break;
+      }
+      if ((w & ~kValMask) == 0) w = ld_volatile(&st[idx]);
+    }
+    if (timed_out) {
+      if (lane == 0) set_status(status, GJ_ERR_TIMEOUT);
+      break;
+    }
+    const unsigned inc = __ballot_sync(0xffffffffu, (w & ~kValMask) == kFlagInc);
+    const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive predecessor in this window
+    uint64_t v = lane <= stop ? (w & kValMask) : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (inc) break;
+    base -= 32;
+  }
+  if (lane == 0) st_volatile(&st[tile], kFlagInc | (excl + agg));
+  __syncwarp();
+  return excl;
+}
+
+// ------------------------------------------------------------------ bulk copies
+// cp.async.bulk global -> shared with completion on an mbarrier (sm_90+). The
+// source address, the shared destination and the size must be multiples of 16
+// bytes; callers copy the aligned body this way and the ragged end with plain
+// loads.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: after kSpinLimit polls the error is recorded and the caller
+// proceeds, so the kernel always ends.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t phase, int* err) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, phase)) {
+    if (++spins > kSpinLimit) {
+      set_status(err, GJ_ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ columns
 struct ColSet {
   const void* src[kMaxCols];

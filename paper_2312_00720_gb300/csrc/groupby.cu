@@ -498,9 +498,12 @@ __global__ void __launch_bounds__(kPgbThreads) pgb_kernel(const K* __restrict__ 
       break;
     }
   }
-  if (threadIdx.x == 0) {
-    s_goff = (int64_t)lookback_scan(pstat, p, (uint64_t)total, err);
-    if (p == nparts - 1) *d_ngroups = s_goff + total;
+  if (threadIdx.x < 32) {
+    const int64_t goff = (int64_t)lookback_scan_warp(pstat, p, (uint64_t)total, err);
+    if (threadIdx.x == 0) {
+      s_goff = goff;
+      if (p == nparts - 1) *d_ngroups = goff + total;
+    }
   }
   __syncthreads();
   if (q < 0) return;

@@ -43,44 +43,6 @@ struct PassDigits {
   int width[16];
 };
 
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: after kSpinLimit polls the error is recorded and the caller
-// proceeds, so the kernel always ends.
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t phase, int* err) {
-  uint32_t spins = 0;
-  while (!mbar_try_wait(bar, phase)) {
-    if (++spins > kSpinLimit) {
-      set_status(err, GJ_ERR_TIMEOUT);
-      return;
-    }
-  }
-}
-
 // Exclusive scan of one value per thread over the block.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -271,28 +233,39 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
     }
     st_volatile32(&a.status[(int64_t)tile * radix + d], (tile == 0 ? kSFlagInc : kSFlagAgg) | tcnt);
   }
-  const uint32_t hv = d < radix ? a.hist[d] : 0;
   const uint32_t tstart = block_excl_scan(tcnt, s_scan);
-  const uint32_t dbase = block_excl_scan(hv, s_scan);
   if (d < radix) {
+    const uint32_t dbase = a.hist[d];  // exclusive prefix of the pass's digit counts
     s_tstart[d] = tstart;
     uint32_t excl = 0;
     if (tile > 0) {
+      // read a window of predecessors per round trip; walk it nearest first
+      constexpr int kWin = 8;
       int64_t t = tile - 1;
       uint32_t spins = 0;
-      while (t >= 0) {
-        const uint32_t w = ld_volatile32(&a.status[t * radix + d]);
-        const uint32_t flag = w & ~kSVal;
-        if (flag == 0) {
-          if (++spins > kSpinLimit) {
-            set_status(a.err, GJ_ERR_TIMEOUT);
+      bool done = false;
+      while (!done && t >= 0) {
+        uint32_t w[kWin];
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) w[k] = t - k >= 0 ? ld_volatile32(&a.status[(t - k) * radix + d]) : kSFlagInc;
+#pragma unroll
+        for (int k = 0; k < kWin; ++k) {
+          while ((w[k] & ~kSVal) == 0) {
+            if (++spins > kSpinLimit) {
+              set_status(a.err, GJ_ERR_TIMEOUT);
+              done = true;
+              break;
+            }
+            w[k] = ld_volatile32(&a.status[(t - k) * radix + d]);
+          }
+          if (done) break;
+          excl += w[k] & kSVal;
+          if ((w[k] & ~kSVal) == kSFlagInc) {
+            done = true;
             break;
           }
-          continue;
         }
-        excl += w & kSVal;
-        if (flag == kSFlagInc) break;
-        --t;
+        t -= kWin;
       }
       st_volatile32(&a.status[(int64_t)tile * radix + d], kSFlagInc | (excl + tcnt));
     }
@@ -313,27 +286,69 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   }
   __syncthreads();
 
-  // ---- write every column in digit-sorted order
-  {
-    K* kout = (K*)a.kout;
-    for (int p = threadIdx.x; p < tile_n; p += kThreads) kout[s_gdst[s_sdig[p]] + p] = s_key[s_inv[p]];
+  // ---- write every column in digit-sorted order. Thread t owns sorted positions
+  // t, t + kThreads, ...: their destinations and source rows are computed once
+  // and reused for every column.
+  uint32_t dst_at[kMaxChunks];
+  uint16_t src_at[kMaxChunks];
+#pragma unroll
+  for (int i = 0; i < kMaxChunks; ++i) {
+    if (i >= a.chunks) break;
+    const int p = threadIdx.x + i * kThreads;
+    if (p < tile_n) {
+      dst_at[i] = (uint32_t)(s_gdst[s_sdig[p]] + p);
+      src_at[i] = s_inv[p];
+    }
   }
-  if (a.bulk) mbar_wait(&s_bar[1], 0, a.err);
-  __syncthreads();
+  {
+    K* __restrict__ kout = (K*)a.kout;
+#pragma unroll
+    for (int i = 0; i < kMaxChunks; ++i) {
+      if (i >= a.chunks) break;
+      if (threadIdx.x + i * kThreads < tile_n) kout[dst_at[i]] = s_key[src_at[i]];
+    }
+  }
+  if (a.bulk) mbar_wait(&s_bar[1], 0, a.err);  // each thread observes the columns' arrival itself
   for (int c = 0; c < a.cols.n; ++c) {
     const bool gen = (a.gen_mask >> c) & 1u;
     if (a.cols.size[c] == 8) {
       const int64_t* st = (const int64_t*)(smem + a.col_off[c]);
-      int64_t* dst = (int64_t*)a.cols.dst[c];
-      for (int p = threadIdx.x; p < tile_n; p += kThreads)
-        dst[s_gdst[s_sdig[p]] + p] = gen ? tile_base + s_inv[p] : st[s_inv[p]];
+      int64_t* __restrict__ dst = (int64_t*)a.cols.dst[c];
+#pragma unroll
+      for (int i = 0; i < kMaxChunks; ++i) {
+        if (i >= a.chunks) break;
+        if (threadIdx.x + i * kThreads < tile_n) dst[dst_at[i]] = gen ? tile_base + src_at[i] : st[src_at[i]];
+      }
     } else {
       const int32_t* st = (const int32_t*)(smem + a.col_off[c]);
-      int32_t* dst = (int32_t*)a.cols.dst[c];
-      for (int p = threadIdx.x; p < tile_n; p += kThreads)
-        dst[s_gdst[s_sdig[p]] + p] = gen ? (int32_t)(tile_base + s_inv[p]) : st[s_inv[p]];
+      int32_t* __restrict__ dst = (int32_t*)a.cols.dst[c];
+#pragma unroll
+      for (int i = 0; i < kMaxChunks; ++i) {
+        if (i >= a.chunks) break;
+        if (threadIdx.x + i * kThreads < tile_n)
+          dst[dst_at[i]] = gen ? (int32_t)(tile_base + src_at[i]) : st[src_at[i]];
+      }
     }
   }
+}
+
+// Digit counts of every pass -> exclusive prefix (the start of each digit's
+// region), in place. One block of 256 threads per pass.
+__global__ void __launch_bounds__(256) radix_bases_kernel(uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s[kRadixMax];
+  uint32_t* h = hist + blockIdx.x * kRadixMax;
+  s[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int d = 0; d < kRadixMax; ++d) {
+      const uint32_t c = s[d];
+      s[d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  h[threadIdx.x] = s[threadIdx.x];
 }
 
 template <typename K>
@@ -415,6 +430,10 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
     LaunchScope ls(ctx, KK_RADIX_HIST);
     radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>(kin, n, pd, transform, hist);
+  }
+  {
+    LaunchScope ls(ctx, KK_RADIX_HIST);
+    radix_bases_kernel<<<plan.passes, 256, 0, s>>>(hist);
   }
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(K) == 8]) {
@@ -575,6 +594,10 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
     const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
     LaunchScope ls(ctx, KK_RADIX_HIST);
     radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>((const K*)in->key, n, pd, transform, scratch);
+  }
+  {
+    LaunchScope ls(ctx, KK_RADIX_HIST);
+    radix_bases_kernel<<<1, 256, 0, s>>>(scratch);
   }
   if ((st = cuda_check(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSmemBudget + 16 * 1024))) != GJ_OK)
