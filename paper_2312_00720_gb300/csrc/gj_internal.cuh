@@ -261,6 +261,54 @@ __device__ __forceinline__ void agg_atomic(int op, int64_t* p, int64_t v) {
   }
 }
 
+// Up to kColCache distinct 4-byte value columns read once per row and shared by
+// every aggregate over them: slot[j] is aggregate j's cached column or -1.
+constexpr int kColCache = 3;
+struct ColCache {
+  int32_t n;
+  const int32_t* src[kColCache];
+  int8_t slot[kMaxAggs];
+};
+
+inline ColCache make_col_cache(const Aggs& A) {
+  ColCache cc{};
+  for (int j = 0; j < A.n; ++j) {
+    cc.slot[j] = -1;
+    if (A.op[j] == GJ_AGG_COUNT || A.size[j] != 4) continue;
+    int s = -1;
+    for (int q = 0; q < cc.n; ++q)
+      if (cc.src[q] == A.src[j]) s = q;
+    if (s < 0 && cc.n < kColCache) {
+      s = cc.n;
+      cc.src[cc.n++] = (const int32_t*)A.src[j];
+    }
+    cc.slot[j] = (int8_t)s;
+  }
+  return cc;
+}
+
+// Loads the cached columns of B rows at once (predicated, no early exit, so all
+// loads are in flight together).
+template <int B>
+__device__ __forceinline__ void load_cached(const ColCache& cc, const int64_t (&row)[B], const bool (&valid)[B],
+                                            int32_t (&cv)[kColCache][B]) {
+#pragma unroll
+  for (int s = 0; s < kColCache; ++s)
+#pragma unroll
+    for (int u = 0; u < B; ++u) cv[s][u] = (s < cc.n && valid[u]) ? __ldcs(cc.src[s] + row[u]) : 0;
+}
+
+template <int B>
+__device__ __forceinline__ int64_t cached_value(const Aggs& A, const ColCache& cc, int j,
+                                                const int32_t (&cv)[kColCache][B], int u, int64_t row) {
+  if (A.op[j] == GJ_AGG_COUNT) return 1;
+  const int s = cc.slot[j];
+  if (s == 0) return cv[0][u];
+  if (s == 1) return cv[1][u];
+  if (s == 2) return cv[2][u];
+  return load_as_i64(A.src[j], A.size[j], row);
+}
+
 // ------------------------------------------------------------------ host side
 struct Ctx {
   cudaStream_t stream;

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 2) phj_probe_agg_kernel(const K* __r
                                                                  const int64_t* __restrict__ roff, int pbits,
                                                                  const K* __restrict__ skey, int64_t ns, GroupSink G,
                                                                  int* tile_counter, int64_t ntiles, int* err) {
-  extern __shared__ __align__(16) unsigned char s_raw[];
+  extern __shared__ __align__(128) unsigned char s_raw[];
   K* s_key = (K*)s_raw;
   int32_t* s_part = (int32_t*)(s_key + kTileS);
   int32_t* s_midx = s_part + kTileS;
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) nphj_probe_agg_kernel(const K* __res
                                                                   const int32_t* __restrict__ ht, uint64_t mask,
                                                                   const K* __restrict__ skey, int64_t ns, GroupSink G,
                                                                   int* err) {
-  extern __shared__ __align__(16) unsigned char s_raw[];
+  extern __shared__ __align__(128) unsigned char s_raw[];
   unsigned long long* s_cnt = (unsigned long long*)s_raw;
   int64_t* s_agg = (int64_t*)(s_cnt + (G.smem ? G.nslots : 0));
   sink_smem_init(G, s_cnt, s_agg);
