@@ -9,13 +9,14 @@
 //     small, contiguous partition R'_p (clustered).
 //   * UR (GFUR, Fig. gfur): (key, tuple id) pairs are partitioned and payloads
 //     are gathered from the untransformed inputs through the ids.
-// The probe side is walked in fixed-size tiles of the partitioned S'. A tile
+// The probe side is walked in fixed-size units of the partitioned S'. A unit
 // covers the tail of one partition, whole partitions or a slice of a large
-// one; each partition slice rebuilds the table of R'_p, which is the paper's
-// decomposition of large probe partitions (Sec. 3.1.2 / 4.1.4) done by
-// construction, so skewed foreign keys do not unbalance the blocks. Output
-// positions come from a decoupled look-back over tiles, so the result is
-// compact, ordered by S' and identical on every run.
+// one; a table of R'_p is built once per unit that holds rows of partition p
+// (the paper's decomposition of large probe partitions, Sec. 3.1.2 / 4.1.4, by
+// construction), so skewed foreign keys do not unbalance the blocks. Output
+// positions come from a decoupled look-back over units, so the result is
+// compact, ordered by S' and identical on every run. The fused join->group-by
+// walks the same partitions in tiles of kTileS rows.
 //
 // NPHJ (Sec. 3.1.3): one global open-addressing table on R (key -> row), S
 // probed in its own order; R payloads are gathered randomly, S sequentially.
@@ -51,22 +52,8 @@ struct JoinIO {
   void* tcols[2 * kMaxCols];
   int64_t cap;
   int64_t* d_count;
-  // staging of the probe tile in shared memory (PHJ): keys, and with GFTR the S'
-  // payload columns, bulk-copied when the block takes its tile
-  int32_t stage_bulk;             // 1: sources 16-byte aligned, use cp.async.bulk
-  int32_t stage_cols;             // 1: S payload columns are staged (GFTR)
-  int32_t scol_off[kMaxCols];     // byte offset of each staged column
-  int32_t stage_bytes;            // bytes of staged columns per tile
-  // GFTR with 4-byte R payloads: each build chunk's payloads are copied into
-  // shared memory (coalesced) and gathered from there
-  int32_t r_stage;
-  int32_t rstage_bytes;
-};
-
-constexpr int kMaxSeg = 32;  // partition slices recorded per probe tile
-
-struct Seg {
-  int32_t p, a, b;
+  int32_t stage_bulk;  // 1: probe keys 16-byte aligned, bulk-copied into shared memory
+  int32_t narrow4;     // 1: every payload column 4 bytes wide, at most 4 per side
 };
 
 template <typename K>
@@ -78,23 +65,18 @@ __device__ __forceinline__ uint32_t smem_slot(K k, int pbits) {
 // Copies g (<= G) consecutive T columns starting at c for the thread's kItems rows.
 template <typename T, int G>
 __device__ __forceinline__ void emit_group(const JoinIO& io, int c, int g, bool rside, const uint32_t* idx,
-                                           const uint32_t* o, const bool* ok, const unsigned char* s_scol) {
+                                           const uint32_t* o, const bool* ok) {
   // loads are unconditional (rows without a match read row 0, which exists), so
   // nothing orders them after one another: all G x kItems are in flight at once.
-  // Staged S columns are read from shared memory at the row's tile position.
   T v[G][kItems];
 #pragma unroll
   for (int q = 0; q < G; ++q) {
     const int cq = c + (q < g ? q : 0);
     const T* __restrict__ src = (const T*)(rside ? io.rsrc[cq] : io.ssrc[cq - io.nr_cols]);
-    const T* st = (!rside && s_scol) ? (const T*)(s_scol + io.scol_off[cq - io.nr_cols]) : nullptr;
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
       const uint32_t r = ok[j] ? idx[j] : 0u;
-      if (st)
-        v[q][j] = st[threadIdx.x + j * kThreads];
-      else
-        v[q][j] = rside ? __ldg(src + r) : __ldcs(src + r);
+      v[q][j] = rside ? __ldg(src + r) : __ldcs(src + r);
     }
   }
 #pragma unroll
@@ -108,41 +90,10 @@ __device__ __forceinline__ void emit_group(const JoinIO& io, int c, int g, bool 
 
 // Compaction + materialisation of one probe tile. s_midx[i] is the matching
 // build row (index into the R-side source arrays, or into r_tid) or -1.
-// R payload columns of the matches in the tile's partition slices, gathered
-// from shared-memory copies of each build chunk (GFTR: R'_p is contiguous).
-__device__ void emit_r_staged(const JoinIO& io, const int64_t* __restrict__ roff, const Seg* segs, int nseg,
-                              const int32_t* s_midx, const int32_t* s_pos, int64_t base, int32_t* s_rstage) {
-  const int t = threadIdx.x;
-  for (int k = 0; k < nseg; ++k) {
-    const Seg sg = segs[k];
-    const int64_t r_lo = roff[sg.p], r_hi = roff[sg.p + 1];
-    for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
-      const int cn = (int)min64(kBuildCap, r_hi - c0);
-      __syncthreads();  // the stage is free
-      for (int c = 0; c < io.nr_cols; ++c) {
-        const int32_t* __restrict__ src = (const int32_t*)io.rsrc[c] + c0;
-#pragma unroll 8
-        for (int j = t; j < cn; j += kThreads) s_rstage[c * kBuildCap + j] = __ldcs(src + j);
-      }
-      __syncthreads();
-      for (int i = sg.a + t; i < sg.b; i += kThreads) {
-        const int32_t m = s_midx[i];
-        if (m < c0 || m >= c0 + cn) continue;
-        const int64_t o = base + s_pos[i];
-        if (o >= io.cap) continue;
-        const int r = (int)(m - c0);
-        for (int c = 0; c < io.nr_cols; ++c) __stcs((int32_t*)io.tcols[c] + o, s_rstage[c * kBuildCap + r]);
-      }
-    }
-  }
-}
-
 template <typename K>
 __device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int tile_n, const K* s_key,
                           const int32_t* s_midx, int32_t* s_pos, const JoinIO& io, uint64_t* tile_status,
-                          int* err, uint32_t* s_scan, uint64_t* s_base, const unsigned char* s_scol = nullptr,
-                          const int64_t* roff = nullptr, const Seg* segs = nullptr, int nseg = -1,
-                          int32_t* s_rstage = nullptr) {
+                          int* err, uint32_t* s_scan, uint64_t* s_base) {
   const int t = threadIdx.x;
   // blocked exclusive scan of match flags
   uint32_t cnt = 0;
@@ -226,8 +177,7 @@ __device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int t
   // columns in groups of one width and side (two 4-byte or one 8-byte column):
   // all loads of a group are in flight before its first store
   const int ncols = io.nr_cols + io.ns_cols;
-  const bool rstaged = io.r_stage && s_rstage && nseg >= 0;
-  int c = rstaged ? io.nr_cols : 0;
+  int c = 0;
   while (c < ncols) {
     const bool rside = c < io.nr_cols;
     const int size = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
@@ -238,97 +188,18 @@ __device__ void emit_tile(int64_t tile, int64_t ntiles, int64_t tile_base, int t
       ++g;
     const uint32_t* idx = rside ? ridx : sidx;
     if (size == 8)
-      emit_group<int64_t, 1>(io, c, g, rside, idx, o, ok, s_scol);
+      emit_group<int64_t, 1>(io, c, g, rside, idx, o, ok);
     else
-      emit_group<int32_t, 2>(io, c, g, rside, idx, o, ok, s_scol);
+      emit_group<int32_t, 2>(io, c, g, rside, idx, o, ok);
     c += g;
   }
-  if (rstaged) emit_r_staged(io, roff, segs, nseg, s_midx, s_pos, base, s_rstage);
 }
 
-template <typename K>
-__device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict__ roff, int pbits,
-                           const K* __restrict__ skey, int64_t tile_base, int tile_n, K* s_key, int32_t* s_part,
-                           int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err, bool keys_staged = false,
-                           Seg* segs = nullptr, int* nseg = nullptr);
-
+// Shared memory of one probe tile walked by probe_tile: probe keys, partition and
+// match of each row, the table and the build chunk's keys.
 template <typename K>
 constexpr size_t phj_smem_bytes() {
   return (size_t)kTileS * sizeof(K) + 2 * (size_t)kTileS * 4 + (size_t)kSlots * 4 + (size_t)kBuildCap * sizeof(K);
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kThreads, 2) phj_probe_kernel(const K* __restrict__ rkey,
-                                                             const int64_t* __restrict__ roff, int pbits,
-                                                             const K* __restrict__ skey, int64_t ns, JoinIO io,
-                                                             uint64_t* tile_status, int* tile_counter, int64_t ntiles,
-                                                             int* err) {
-  extern __shared__ __align__(128) unsigned char s_raw[];
-  K* s_key = (K*)s_raw;                                   // kTileS probe keys
-  unsigned char* s_scol = s_raw + kTileS * sizeof(K);     // staged S' payload columns (io.stage_bytes)
-  int32_t* s_part = (int32_t*)(s_scol + io.stage_bytes);  // partition of each probe row, later its output position
-  int32_t* s_midx = s_part + kTileS;                      // matching build row or -1
-  int32_t* s_slots = s_midx + kTileS;                     // table: build row + 1, 0 = empty
-  K* s_rkey = (K*)(s_slots + kSlots);                     // keys of the build chunk
-  int32_t* s_rstage = (int32_t*)(s_rkey + kBuildCap);     // R payloads of one build chunk (io.rstage_bytes)
-  __shared__ uint32_t s_scan[kThreads / 32];
-  __shared__ uint64_t s_base;
-  __shared__ int64_t s_tile;
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ Seg s_seg[kMaxSeg];
-  __shared__ int s_nseg;
-
-  const int t = threadIdx.x;
-  if (t == 0) {
-    s_tile = atomicAdd(tile_counter, 1);
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  const int64_t tile = s_tile;
-  const int64_t tile_base = tile * kTileS;
-  const int tile_n = (int)min64(kTileS, ns - tile_base);
-
-  // ---- stage the tile: keys on barrier 0, payload columns on barrier 1; they
-  // arrive while the build side is loaded and the tables are built
-  const int ncs = io.stage_cols ? io.ns_cols : 0;
-  int key_from = 0;
-  int col_from[kMaxCols];
-  for (int c = 0; c < ncs; ++c) col_from[c] = 0;
-  if (io.stage_bulk) {
-    const uint32_t kb = ((uint32_t)tile_n * sizeof(K)) & ~15u;
-    key_from = (int)(kb / sizeof(K));
-    for (int c = 0; c < ncs; ++c) col_from[c] = (int)((((uint32_t)tile_n * io.ssize[c]) & ~15u) / io.ssize[c]);
-    if (t == 0) {
-      mbar_expect_tx(&s_bar[0], kb);
-      if (kb) bulk_g2s(s_key, skey + tile_base, kb, &s_bar[0]);
-      uint32_t cb = 0;
-      for (int c = 0; c < ncs; ++c) cb += (uint32_t)col_from[c] * io.ssize[c];
-      mbar_expect_tx(&s_bar[1], cb);
-      for (int c = 0; c < ncs; ++c)
-        if (col_from[c])
-          bulk_g2s(s_scol + io.scol_off[c], (const unsigned char*)io.ssrc[c] + tile_base * io.ssize[c],
-                   (uint32_t)col_from[c] * io.ssize[c], &s_bar[1]);
-    }
-  }
-  for (int i = key_from + t; i < tile_n; i += kThreads) s_key[i] = skey[tile_base + i];
-  for (int c = 0; c < ncs; ++c) {
-    if (io.ssize[c] == 8) {
-      for (int i = col_from[c] + t; i < tile_n; i += kThreads)
-        ((int64_t*)(s_scol + io.scol_off[c]))[i] = ((const int64_t*)io.ssrc[c])[tile_base + i];
-    } else {
-      for (int i = col_from[c] + t; i < tile_n; i += kThreads)
-        ((int32_t*)(s_scol + io.scol_off[c]))[i] = ((const int32_t*)io.ssrc[c])[tile_base + i];
-    }
-  }
-  if (io.stage_bulk) mbar_wait(&s_bar[0], 0, err);
-  __syncthreads();
-  probe_tile<K>(rkey, roff, pbits, skey, tile_base, tile_n, s_key, s_part, s_midx, s_slots, s_rkey, err, true, s_seg,
-                &s_nseg);
-  if (io.stage_bulk && ncs) mbar_wait(&s_bar[1], 0, err);
-  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_part, io, tile_status, err, s_scan, &s_base,
-               ncs ? s_scol : nullptr, roff, s_seg, s_nseg, io.r_stage ? s_rstage : nullptr);
 }
 
 // Finds, for every probe row of S'[tile_base, tile_base + tile_n), the build row
@@ -337,14 +208,12 @@ __global__ void __launch_bounds__(kThreads, 2) phj_probe_kernel(const K* __restr
 template <typename K>
 __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict__ roff, int pbits,
                            const K* __restrict__ skey, int64_t tile_base, int tile_n, K* s_key, int32_t* s_part,
-                           int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err, bool keys_staged, Seg* segs,
-                           int* nseg) {
+                           int32_t* s_midx, int32_t* s_slots, K* s_rkey, int* err) {
   const int t = threadIdx.x;
-  if (nseg && t == 0) *nseg = 0;
   const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
 #pragma unroll 8
   for (int i = t; i < tile_n; i += kThreads) {
-    K k = keys_staged ? s_key[i] : __ldcs(skey + tile_base + i);
+    K k = __ldcs(skey + tile_base + i);
     s_key[i] = k;
     s_part[i] = (int32_t)((uint32_t)KeyTraits<K>::hash64(k) & pmask);
     s_midx[i] = -1;
@@ -362,11 +231,6 @@ __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict
     }
     const int b = lo;
     const int64_t r_lo = roff[p], r_hi = roff[p + 1];
-    if (nseg && t == 0) {
-      // more slices than recorded: the emit gathers from global memory instead
-      if (*nseg >= 0 && *nseg < kMaxSeg && r_hi > r_lo) segs[(*nseg)++] = Seg{p, a, b};
-      else if (r_hi > r_lo) *nseg = -1;
-    }
     for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
       const int cn = (int)min64(kBuildCap, r_hi - c0);
       for (int j = t; j < kSlots; j += kThreads) s_slots[j] = 0;
@@ -407,6 +271,271 @@ __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict
     a = b;
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------- PHJ probe by units
+// A block takes a unit of kUnitRows consecutive rows of S' (taken in order from a
+// counter). Phase 1 walks the unit in sub-tiles of kTileS rows whose keys arrive
+// by bulk copy into a double buffer (the next sub-tile's copy is in flight while
+// the current one is probed) and finds each row's build row; the table of the
+// partition last built stays resident, so a partition spanning sub-tiles is
+// built once per unit. Phase 2 takes the unit's output offset from a decoupled
+// look-back over units and materialises the matches: every warp owns a
+// contiguous range of the unit and writes it without block barriers, all loads
+// of a group of columns in flight before its stores.
+constexpr int kUnitSub = 2;                   // sub-tiles per unit
+constexpr int kUnitRows = kUnitSub * kTileS;  // probe rows per unit
+constexpr int kEmitU = 4;                     // rows per lane per emit step
+
+template <typename K>
+constexpr size_t phj_unit_smem_bytes() {
+  return (size_t)kUnitRows * 4 + 2 * (size_t)kTileS * sizeof(K) + (size_t)kSlots * 4 + (size_t)kBuildCap * sizeof(K);
+}
+
+// T columns c .. c + g - 1 (g <= G, one side and one width) for U rows per lane:
+// every load is issued before the first store. Rows without a match load row 0.
+template <typename T, int G, int U>
+__device__ __forceinline__ void emit_cols(const JoinIO& io, int c, int g, bool rside, const uint32_t (&idx)[U],
+                                          const uint32_t (&o)[U], const bool (&ok)[U]) {
+  T v[G][U];
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    const int cq = c + (q < g ? q : 0);
+    const T* __restrict__ src = (const T*)(rside ? io.rsrc[cq] : io.ssrc[cq - io.nr_cols]);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const uint32_t r = ok[j] ? idx[j] : 0u;
+      v[q][j] = rside ? __ldg(src + r) : __ldcs(src + r);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    T* __restrict__ dst = (T*)io.tcols[c + (q < g ? q : 0)];
+#pragma unroll
+    for (int j = 0; j < U; ++j)
+      if (q < g && ok[j]) __stcs(dst + o[j], v[q][j]);
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restrict__ rkey,
+                                                            const int64_t* __restrict__ roff, int pbits,
+                                                            const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                            uint64_t* unit_status, int* unit_counter, int64_t nunits,
+                                                            int* err) {
+  extern __shared__ __align__(128) unsigned char s_raw[];
+  int32_t* s_midx = (int32_t*)s_raw;                 // kUnitRows: matching build row or -1
+  K* s_kbuf = (K*)(s_midx + kUnitRows);              // 2 x kTileS probe keys
+  int32_t* s_slots = (int32_t*)(s_kbuf + 2 * kTileS);  // table: build row + 1, 0 = empty
+  K* s_rkey = (K*)(s_slots + kSlots);                 // keys of the resident build chunk
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int64_t s_unit;
+  __shared__ uint32_t s_wcnt[kThreads / 32];
+  __shared__ uint64_t s_base;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) {
+    s_unit = atomicAdd(unit_counter, 1);
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int64_t unit = s_unit;
+  if (unit >= nunits) return;
+  const int64_t u0 = unit * kUnitRows;
+  const int un = (int)min64(kUnitRows, ns - u0);
+  const int nsub = (un + kTileS - 1) / kTileS;
+  const uint32_t pmask = pbits >= 32 ? 0xffffffffu : ((1u << pbits) - 1);
+
+  // ---- phase 1: build rows of every probe row of the unit
+  // the 16-byte aligned body of sub-tile k's keys is bulk-copied into buffer k & 1
+  auto body_rows = [&](int k) {
+    const int rows = min(kTileS, un - k * kTileS);
+    return io.stage_bulk ? (int)((((uint32_t)rows * sizeof(K)) & ~15u) / sizeof(K)) : 0;
+  };
+  if (t == 0) {
+    const uint32_t kb = (uint32_t)body_rows(0) * sizeof(K);
+    mbar_expect_tx(&s_bar[0], kb);
+    if (kb) bulk_g2s(s_kbuf, skey + u0, kb, &s_bar[0]);
+  }
+  int64_t cur_p = -1;  // partition whose whole build side is in the table
+  for (int k = 0; k < nsub; ++k) {
+    const int rows = min(kTileS, un - k * kTileS);
+    K* kb = s_kbuf + (k & 1) * kTileS;
+    int32_t* mid = s_midx + k * kTileS;
+    const int64_t sbase = u0 + (int64_t)k * kTileS;
+    __syncthreads();  // sub-tile k - 1 is done with its buffer: it takes sub-tile k + 1
+    if (t == 0 && k + 1 < nsub) {
+      fence_proxy_async();  // the buffer's previous contents were read and written by threads
+      const uint32_t nb = (uint32_t)body_rows(k + 1) * sizeof(K);
+      mbar_expect_tx(&s_bar[(k + 1) & 1], nb);
+      if (nb) bulk_g2s(s_kbuf + ((k + 1) & 1) * kTileS, skey + sbase + kTileS, nb, &s_bar[(k + 1) & 1]);
+    }
+    for (int i = body_rows(k) + t; i < rows; i += kThreads) kb[i] = skey[sbase + i];
+    mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), err);
+    __syncthreads();
+    for (int i = t; i < rows; i += kThreads) mid[i] = -1;
+    __syncthreads();
+    // the partitions present in the sub-tile (non-decreasing in S')
+    auto part_of = [&](int i) { return (uint32_t)KeyTraits<K>::hash64(kb[i]) & pmask; };
+    int a = 0;
+    while (a < rows) {
+      const uint32_t p = part_of(a);
+      int lo = a, hi = rows;  // first row with partition > p
+      while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (part_of(m) <= p) lo = m + 1; else hi = m;
+      }
+      const int b = lo;
+      const int64_t r_lo = roff[p], r_hi = roff[p + 1];
+      const bool whole = r_hi - r_lo <= kBuildCap;
+      for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
+        const int cn = (int)min64(kBuildCap, r_hi - c0);
+        if (!(whole && p == cur_p)) {
+          for (int j = t; j < kSlots; j += kThreads) s_slots[j] = 0;
+#pragma unroll 8
+          for (int j = t; j < cn; j += kThreads) s_rkey[j] = __ldg(rkey + c0 + j);
+          __syncthreads();
+          for (int j = t; j < cn; j += kThreads) {
+            const K kk = s_rkey[j];
+            uint32_t sl = smem_slot<K>(kk, pbits);
+            for (int probe = 0; probe < kSlots; ++probe) {
+              const int prev = atomicCAS(&s_slots[sl], 0, j + 1);
+              if (prev == 0) break;
+              if (s_rkey[prev - 1] == kk) {
+                set_status(err, GJ_ERR_DUPLICATE_KEY);
+                break;
+              }
+              sl = (sl + 1) & (kSlots - 1);
+            }
+          }
+          __syncthreads();
+        }
+        for (int i = a + t; i < b; i += kThreads) {
+          const K kk = kb[i];
+          uint32_t sl = smem_slot<K>(kk, pbits);
+          for (int probe = 0; probe < kSlots; ++probe) {
+            const int v = s_slots[sl];
+            if (v == 0) break;
+            if (s_rkey[v - 1] == kk) {
+              if (mid[i] >= 0) set_status(err, GJ_ERR_DUPLICATE_KEY);
+              mid[i] = (int32_t)(c0 + v - 1);
+              break;
+            }
+            sl = (sl + 1) & (kSlots - 1);
+          }
+        }
+        __syncthreads();  // the table may be rebuilt next
+      }
+      if (r_hi > r_lo) cur_p = whole ? (int64_t)p : -1;
+      a = b;
+    }
+  }
+
+  // ---- unit offset: per-warp match counts over warp-contiguous ranges, look-back
+  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
+  const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
+  uint32_t cnt = 0;
+  for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_wcnt[warp] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
+    if (lane == 0) {
+      s_base = excl;
+      if (unit == nunits - 1 && io.d_count) *io.d_count = (int64_t)(excl + tot);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: each warp materialises its range, no block barriers
+  int64_t pos = (int64_t)s_base;
+  for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+  const int64_t cap = io.cap;
+  const unsigned lt = (1u << lane) - 1;
+  const int ncols = io.nr_cols + io.ns_cols;
+  bool overflow = false;
+  for (int b0 = w0; b0 < wend; b0 += 32 * kEmitU) {
+    uint32_t o[kEmitU], ridx[kEmitU], sidx[kEmitU];
+    bool ok[kEmitU];
+#pragma unroll
+    for (int j = 0; j < kEmitU; ++j) {
+      const int r = b0 + j * 32 + lane;
+      const int32_t m = r < wend ? s_midx[r] : -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, m >= 0);
+      const int64_t oo = pos + __popc(bal & lt);
+      pos += __popc(bal);
+      ok[j] = m >= 0 && oo < cap;
+      overflow |= m >= 0 && oo >= cap;
+      o[j] = (uint32_t)oo;
+      ridx[j] = (uint32_t)m;
+      sidx[j] = (uint32_t)(u0 + r);
+    }
+    if (io.r_tid) {
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) ridx[j] = ok[j] ? (uint32_t)__ldg(io.r_tid + ridx[j]) : 0u;
+    }
+    if (io.s_tid) {
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) sidx[j] = ok[j] ? (uint32_t)__ldcs(io.s_tid + sidx[j]) : 0u;
+    }
+    {
+      K kv[kEmitU];
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) kv[j] = skey[ok[j] ? u0 + b0 + j * 32 + lane : u0];
+      K* __restrict__ tk = (K*)io.tkey;
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j)
+        if (ok[j]) __stcs(tk + o[j], kv[j]);
+    }
+    if (io.narrow4) {
+      // every column 4 bytes wide, at most 4 per side: all loads of the step in flight together
+      int32_t vr[4][kEmitU], vs[4][kEmitU];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t* __restrict__ rs = (const int32_t*)io.rsrc[q < io.nr_cols ? q : 0];
+        const int32_t* __restrict__ ss = (const int32_t*)io.ssrc[q < io.ns_cols ? q : 0];
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          vr[q][j] = q < io.nr_cols ? __ldg(rs + (ok[j] ? ridx[j] : 0u)) : 0;
+          vs[q][j] = q < io.ns_cols ? __ldcs(ss + (ok[j] ? sidx[j] : 0u)) : 0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int32_t* __restrict__ dr = (int32_t*)io.tcols[q < io.nr_cols ? q : 0];
+        int32_t* __restrict__ ds = (int32_t*)io.tcols[io.nr_cols + (q < io.ns_cols ? q : 0)];
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          if (q < io.nr_cols && ok[j]) __stcs(dr + o[j], vr[q][j]);
+          if (q < io.ns_cols && ok[j]) __stcs(ds + o[j], vs[q][j]);
+        }
+      }
+      continue;
+    }
+    int c = 0;
+    while (c < ncols) {
+      const bool rside = c < io.nr_cols;
+      const int size = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
+      const int gmax = size == 8 ? 2 : 4;
+      int g = 1;
+      while (g < gmax && c + g < ncols && (c + g < io.nr_cols) == rside &&
+             (rside ? io.rsize[c + g] : io.ssize[c + g - io.nr_cols]) == size)
+        ++g;
+      if (size == 8)
+        emit_cols<int64_t, 2, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
+      else
+        emit_cols<int32_t, 4, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
+      c += g;
+    }
+  }
+  if (overflow) set_status(err, GJ_ERR_CAPACITY);
 }
 
 // ---------------------------------------------------------------- NPHJ
@@ -818,36 +947,26 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if (scr.failed()) return GJ_ERR_OOM;
   if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, nr, 0, bits, kHashed, roff)) != GJ_OK)
     return st;
-  // stage the probe tile's keys (and with GFTR its payload columns) in shared memory
-  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  io.stage_cols = gftr ? 1 : 0;
-  {
-    int off = 0;
-    for (int c = 0; c < S->ncols; ++c) {
-      io.scol_off[c] = off;
-      off += kTileS * io.ssize[c];
-    }
-    io.stage_bytes = io.stage_cols ? off : 0;
-    bool al = al16(sk);
-    if (io.stage_cols)
-      for (int c = 0; c < S->ncols; ++c) al = al && al16(io.ssrc[c]);
-    io.stage_bulk = al ? 1 : 0;
-  }
-  // Copying each build chunk's payloads to shared memory and gathering there was
-  // measured slower than gathering through L1 on this workload (6.6 vs 4.6 ms for
-  // the full-size probe); the path stays available but is off.
-  io.r_stage = 0;
-  io.rstage_bytes = 0;
-  const size_t dyn = phj_smem_bytes<K>() + io.stage_bytes + io.rstage_bytes;
+  // probe keys arrive by bulk copy when S' keys are 16-byte aligned
+  io.stage_bulk = (reinterpret_cast<uintptr_t>(sk) & 15) == 0 ? 1 : 0;
+  io.narrow4 = io.nr_cols >= 1 && io.nr_cols <= 4 && io.ns_cols >= 1 && io.ns_cols <= 4;
+  for (int c = 0; c < io.nr_cols; ++c) io.narrow4 &= io.rsize[c] == 4;
+  for (int c = 0; c < io.ns_cols; ++c) io.narrow4 &= io.ssize[c] == 4;
+  const int64_t nunits = (ns + kUnitRows - 1) / kUnitRows;
+  uint64_t* ustat = scr.get_as<uint64_t>(nunits);
+  int* ucounter = scr.get_as<int>(1);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = cuda_check(cudaMemsetAsync(ustat, 0, sizeof(uint64_t) * nunits, s))) != GJ_OK) return st;
+  if ((st = cuda_check(cudaMemsetAsync(ucounter, 0, sizeof(int), s))) != GJ_OK) return st;
+  const size_t dyn = phj_unit_smem_bytes<K>();
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(phj_probe_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(phj_smem_bytes<K>() + (size_t)kMaxCols * kTileS * 8 + kBuildCap * 16));
+    cudaFuncSetAttribute(phj_unit_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     attr_set[sizeof(K) == 8] = true;
   }
   LaunchScope ls(ctx, KK_PHJ_PROBE);
-  phj_probe_kernel<K><<<(unsigned)ntiles, kThreads, dyn, s>>>(rk, roff, bits, sk, ns, io, tstat, counter, ntiles,
-                                                               ctx.d_status);
+  phj_unit_kernel<K><<<(unsigned)nunits, kThreads, dyn, s>>>(rk, roff, bits, sk, ns, io, ustat, ucounter, nunits,
+                                                              ctx.d_status);
   return cuda_check(cudaGetLastError());
 }
 
