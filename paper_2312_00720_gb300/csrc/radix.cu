@@ -31,7 +31,7 @@ namespace {
 constexpr int kRadixMax = 256;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxChunks = 16;  // 32-row chunks per warp: tiles of up to 8192 rows
+constexpr int kMaxChunks = 8;  // 32-row chunks per warp: tiles of up to 4096 rows
 constexpr uint32_t kSFlagAgg = 1u << 30;
 constexpr uint32_t kSFlagInc = 2u << 30;
 constexpr uint32_t kSVal = (1u << 30) - 1;
