@@ -29,19 +29,12 @@ namespace gj {
 namespace {
 
 constexpr int kRadixMax = 256;
+constexpr int kHistThreads = 256;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChunks = 8;  // 32-row chunks per warp: tiles of up to 4096 rows
-constexpr uint32_t kSFlagAgg = 1u << 30;
-constexpr uint32_t kSFlagInc = 2u << 30;
-constexpr uint32_t kSVal = (1u << 30) - 1;
 constexpr int kSmemBudget = 100 * 1024;  // in-stage + per-row arrays; two blocks per SM
 
-struct PassDigits {
-  int passes;
-  int shift[16];
-  int width[16];
-};
 
 // Exclusive scan of one value per thread over the block.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp) {
@@ -69,38 +62,122 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
   return before + x - v;
 }
 
-// ---------------------------------------------------------------- histogram
+// ---------------------------------------------------------------- tile histograms
+// Digit counts of every tile of tile_rows rows: tcount[d * ld + tile] (ld >= ntiles,
+// a multiple of 4); the digit totals are added into total[d] (zeroed by the
+// caller). Blocks stride over the tiles.
 template <typename K>
-__global__ void __launch_bounds__(256) radix_hist_kernel(const K* __restrict__ kin, int64_t n, PassDigits pd,
-                                                         int transform, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[16][kRadixMax];
-  for (int i = threadIdx.x; i < pd.passes * kRadixMax; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  // 16-byte vector loads over the aligned body, scalar loads for the ragged ends
+__global__ void __launch_bounds__(kHistThreads) tile_hist_kernel(const K* __restrict__ kin, int64_t n, int shift,
+                                                                  int width, int transform, int tile_rows,
+                                                                  int64_t ld, uint32_t* __restrict__ tcount,
+                                                                  uint32_t* __restrict__ total) {
+  __shared__ uint32_t s_h[kRadixMax];
+  __shared__ uint32_t s_tot[kRadixMax];
+  const int radix = 1 << width;
+  const int64_t ntiles = (n + tile_rows - 1) / tile_rows;
   constexpr int kVec = 16 / sizeof(K);
-  const uintptr_t addr = reinterpret_cast<uintptr_t>(kin);
-  int64_t head = (int64_t)(((16 - (addr & 15)) & 15) / sizeof(K));
-  if ((addr % sizeof(K)) != 0 || head > n) head = n;
-  const int64_t nvec = (n - head) / kVec;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  auto count = [&](K k) {
-    for (int q = 0; q < pd.passes; ++q)
-      atomicAdd(&sh[q][extract_digit<K>(k, transform, pd.shift[q], pd.width[q])], 1u);
-  };
-  const uint4* body = reinterpret_cast<const uint4*>(kin + head);
-  for (int64_t v = tid; v < nvec; v += stride) {
-    uint4 u = __ldcs(body + v);
-    const K* ks = reinterpret_cast<const K*>(&u);
+  const bool vec = (reinterpret_cast<uintptr_t>(kin) & 15) == 0;  // tile_rows * sizeof(K) is a multiple of 16
+  for (int d = threadIdx.x; d < radix; d += kHistThreads) s_tot[d] = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int d = threadIdx.x; d < radix; d += kHistThreads) s_h[d] = 0;
+    __syncthreads();
+    const int64_t tb = tile * tile_rows;
+    const int tn = (int)min64(tile_rows, n - tb);
+    const K* kt = kin + tb;
+    int from = 0;
+    if (vec) {
+      const int nvec = tn / kVec;
+      const uint4* body = reinterpret_cast<const uint4*>(kt);
+      // all of a thread's loads first, then its counts
+      constexpr int kLoads = 4;
+      for (int v0 = 0; v0 < nvec; v0 += kLoads * kHistThreads) {
+        uint4 u[kLoads];
 #pragma unroll
-    for (int e = 0; e < kVec; ++e) count(ks[e]);
+        for (int q = 0; q < kLoads; ++q) {
+          const int v = v0 + q * kHistThreads + threadIdx.x;
+          u[q] = v < nvec ? __ldcs(body + v) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < kLoads; ++q) {
+          if (v0 + q * kHistThreads + threadIdx.x >= nvec) continue;
+          const K* ks = reinterpret_cast<const K*>(&u[q]);
+#pragma unroll
+          for (int e = 0; e < kVec; ++e) atomicAdd(&s_h[extract_digit<K>(ks[e], transform, shift, width)], 1u);
+        }
+      }
+      from = nvec * kVec;
+    }
+    for (int r = from + threadIdx.x; r < tn; r += kHistThreads)
+      atomicAdd(&s_h[extract_digit<K>(kt[r], transform, shift, width)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += kHistThreads) {
+      const uint32_t c = s_h[d];
+      tcount[(int64_t)d * ld + tile] = c;
+      s_tot[d] += c;
+    }
   }
-  for (int64_t i = tid; i < head; i += stride) count(kin[i]);
-  for (int64_t i = head + nvec * kVec + tid; i < n; i += stride) count(kin[i]);
   __syncthreads();
-  for (int i = threadIdx.x; i < pd.passes * kRadixMax; i += blockDim.x) {
-    uint32_t c = (&sh[0][0])[i];
-    if (c) atomicAdd(&hist[i], c);
+  for (int d = threadIdx.x; d < radix; d += kHistThreads)
+    if (s_tot[d]) atomicAdd(&total[d], s_tot[d]);
+}
+
+// In place: tcount[d * ld + t] -> the output position of tile t's first row with
+// digit d = (rows of digits < d) + (rows with digit d in tiles < t). One block per
+// digit; each thread scans a contiguous chunk of tiles, a multiple of 4 long, read
+// and written with 16-byte accesses.
+__global__ void __launch_bounds__(1024) tile_offsets_kernel(uint32_t* __restrict__ tcount,
+                                                            const uint32_t* __restrict__ total, int64_t ld) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_base;
+  const int d = blockIdx.x;
+  if (threadIdx.x < 32) {
+    uint32_t b = 0;
+    for (int e = threadIdx.x; e < d; e += 32) b += total[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (threadIdx.x == 0) s_base = b;
+  }
+  uint4* row = reinterpret_cast<uint4*>(tcount + (int64_t)d * ld);
+  // entries past ntiles come after every real tile: what they hold changes no real offset
+  const int64_t nv = ld / 4;
+  const int64_t chunk = (nv + blockDim.x - 1) / blockDim.x;
+  const int64_t v0 = min64((int64_t)threadIdx.x * chunk, nv), v1 = min64(v0 + chunk, nv);
+  uint32_t sum = 0;
+#pragma unroll 4
+  for (int64_t v = v0; v < v1; ++v) {
+    const uint4 u = row[v];
+    sum += u.x + u.y + u.z + u.w;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = s_base + (warp ? s_warp[warp - 1] : 0u) + x - sum;
+#pragma unroll 4
+  for (int64_t v = v0; v < v1; ++v) {
+    uint4 u = row[v];
+    uint4 o;
+    o.x = run;
+    o.y = run + u.x;
+    o.z = o.y + u.y;
+    o.w = o.z + u.z;
+    run = o.w + u.w;
+    row[v] = o;
   }
 }
 
@@ -112,9 +189,8 @@ struct ScatterArgs {
   uint32_t gen_mask;  // columns whose values are the input row index (tuple ids)
   int64_t n;
   int shift, width, transform;
-  const uint32_t* hist;  // 2^width global digit counts of this pass
-  uint32_t* status;      // tiles x 2^width look-back words
-  int* tile_counter;
+  const uint32_t* offs;  // [2^width][ld]: output position of each tile's first row of each digit
+  int64_t ld;
   int* err;
   int tile_rows;  // 512 * chunks
   int chunks;     // 32-row chunks per warp
@@ -135,7 +211,6 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   __shared__ uint32_t s_tstart[kRadixMax];
   __shared__ int64_t s_gdst[kRadixMax];
   __shared__ uint32_t s_scan[kWarps];
-  __shared__ int s_tile;
   __shared__ __align__(8) uint64_t s_bar[2];
 
   const int radix = 1 << a.width;
@@ -147,13 +222,12 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   uint16_t* s_wcnt = (uint16_t*)(smem + a.wcnt_off);  // [kWarps][kRadixMax]
 
   if (threadIdx.x == 0) {
-    s_tile = atomicAdd(a.tile_counter, 1);
     mbar_init(&s_bar[0], 1);
     mbar_init(&s_bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  const int tile = s_tile;
+  const int64_t tile = blockIdx.x;
   const int64_t tile_base = (int64_t)tile * a.tile_rows;
   const int tile_n = (int)min64(a.tile_rows, a.n - tile_base);
 
@@ -221,7 +295,8 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   }
   __syncthreads();
 
-  // ---- per digit: warp offsets, tile count, publish, global offsets
+  // ---- per digit: warp offsets, tile count, tile-local starts; the tile's output
+  // position for each digit comes from the tile histograms of the pass
   const int d = threadIdx.x;
   uint32_t tcnt = 0;
   if (d < radix) {
@@ -231,45 +306,11 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
       s_wcnt[w * kRadixMax + d] = (uint16_t)tcnt;
       tcnt += c;
     }
-    st_volatile32(&a.status[(int64_t)tile * radix + d], (tile == 0 ? kSFlagInc : kSFlagAgg) | tcnt);
   }
   const uint32_t tstart = block_excl_scan(tcnt, s_scan);
   if (d < radix) {
-    const uint32_t dbase = a.hist[d];  // exclusive prefix of the pass's digit counts
     s_tstart[d] = tstart;
-    uint32_t excl = 0;
-    if (tile > 0) {
-      // read a window of predecessors per round trip; walk it nearest first
-      constexpr int kWin = 8;
-      int64_t t = tile - 1;
-      uint32_t spins = 0;
-      bool done = false;
-      while (!done && t >= 0) {
-        uint32_t w[kWin];
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) w[k] = t - k >= 0 ? ld_volatile32(&a.status[(t - k) * radix + d]) : kSFlagInc;
-#pragma unroll
-        for (int k = 0; k < kWin; ++k) {
-          while ((w[k] & ~kSVal) == 0) {
-            if (++spins > kSpinLimit) {
-              set_status(a.err, GJ_ERR_TIMEOUT);
-              done = true;
-              break;
-            }
-            w[k] = ld_volatile32(&a.status[(t - k) * radix + d]);
-          }
-          if (done) break;
-          excl += w[k] & kSVal;
-          if ((w[k] & ~kSVal) == kSFlagInc) {
-            done = true;
-            break;
-          }
-        }
-        t -= kWin;
-      }
-      st_volatile32(&a.status[(int64_t)tile * radix + d], kSFlagInc | (excl + tcnt));
-    }
-    s_gdst[d] = (int64_t)dbase + excl - tstart;
+    s_gdst[d] = (int64_t)a.offs[(int64_t)d * a.ld + tile] - tstart;
   }
   __syncthreads();
 
@@ -332,25 +373,6 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   }
 }
 
-// Digit counts of every pass -> exclusive prefix (the start of each digit's
-// region), in place. One block of 256 threads per pass.
-__global__ void __launch_bounds__(256) radix_bases_kernel(uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s[kRadixMax];
-  uint32_t* h = hist + blockIdx.x * kRadixMax;
-  s[threadIdx.x] = h[threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int d = 0; d < kRadixMax; ++d) {
-      const uint32_t c = s[d];
-      s[d] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  h[threadIdx.x] = s[threadIdx.x];
-}
-
 template <typename K>
 __global__ void bounds_kernel(const K* __restrict__ keys, int64_t n, int shift, int width, int transform,
                               int64_t* __restrict__ off) {
@@ -370,12 +392,6 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
                                 int64_t n, int lo, int hi, int transform, int bits_per_pass) {
   RadixPlan plan = make_radix_plan(lo, hi, bits_per_pass);
   if (n == 0) return GJ_OK;
-  PassDigits pd;
-  pd.passes = plan.passes;
-  for (int q = 0; q < plan.passes; ++q) {
-    pd.shift[q] = plan.shift[q];
-    pd.width[q] = plan.width[q];
-  }
   uint32_t gen_mask = 0;
   int row_bytes = sizeof(K);  // generated tuple ids are staged from the second pass on: count them
   for (int c = 0; c < cols_in.n; ++c) {
@@ -408,10 +424,9 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   off += kWarps * kRadixMax * 2;
   const size_t dyn = (size_t)off;
 
-  uint32_t* hist = scr.get_as<uint32_t>((size_t)plan.passes * kRadixMax);
-  const size_t status_words = (size_t)tiles * kRadixMax;
-  uint32_t* status = scr.get_as<uint32_t>(status_words * plan.passes);
-  int* counters = scr.get_as<int>(plan.passes);
+  uint32_t* total = scr.get_as<uint32_t>((size_t)plan.passes * kRadixMax);
+  const int64_t ld = (tiles + 3) & ~int64_t(3);                      // row stride of the tile offsets
+  uint32_t* offs = scr.get_as<uint32_t>((size_t)ld * kRadixMax);     // reused by every pass
   K* ktmp = nullptr;
   ColSet tmp = cols_in;
   if (plan.passes > 1) {
@@ -421,20 +436,7 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   if (scr.failed()) return GJ_ERR_OOM;
   cudaStream_t s = ctx.stream;
   gj_status st;
-  if ((st = cuda_check(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * plan.passes * kRadixMax, s))) != GJ_OK) return st;
-  if ((st = cuda_check(cudaMemsetAsync(status, 0, sizeof(uint32_t) * status_words * plan.passes, s))) != GJ_OK)
-    return st;
-  if ((st = cuda_check(cudaMemsetAsync(counters, 0, sizeof(int) * plan.passes, s))) != GJ_OK) return st;
-
-  {
-    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
-    LaunchScope ls(ctx, KK_RADIX_HIST);
-    radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>(kin, n, pd, transform, hist);
-  }
-  {
-    LaunchScope ls(ctx, KK_RADIX_HIST);
-    radix_bases_kernel<<<plan.passes, 256, 0, s>>>(hist);
-  }
+  if ((st = cuda_check(cudaMemsetAsync(total, 0, sizeof(uint32_t) * plan.passes * kRadixMax, s))) != GJ_OK) return st;
   static bool attr_set[2] = {false, false};
   if (!attr_set[sizeof(K) == 8]) {
     cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
@@ -456,10 +458,20 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     a.bulk = bulk ? 1 : 0;
     a.shift = plan.shift[q];
     a.width = plan.width[q];
-    a.hist = hist + q * kRadixMax;
-    a.status = status + status_words * q;
-    a.tile_counter = counters + q;
+    a.offs = offs;
+    a.ld = ld;
     a.err = ctx.d_status;
+    {
+      // where each tile's rows of each digit go: tile histograms, then their scan
+      LaunchScope ls(ctx, KK_RADIX_HIST);
+      const unsigned hb = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx.num_sms * 8);
+      tile_hist_kernel<K><<<hb, kHistThreads, 0, s>>>((const K*)a.kin, n, a.shift, a.width, transform, tile_rows, ld,
+                                                      offs, total + q * kRadixMax);
+    }
+    {
+      LaunchScope ls(ctx, KK_RADIX_HIST);
+      tile_offsets_kernel<<<1u << a.width, 1024, 0, s>>>(offs, total + q * kRadixMax, ld);
+    }
     if (q > 0 && gen_mask) {
       // tuple ids now sit in shared memory like any other column
       int o = tile_rows * (int)sizeof(K);
@@ -518,13 +530,13 @@ gj_status radix_partition_run(const Ctx& ctx, Scratch& scr, int key_type, const 
 
 // ---------------------------------------------------------------- allocation-free variant
 // For callers that cannot allocate device memory: a single-pass partition whose
-// scratch (digit histogram, tile counter, look-back words) is this file-scope
+// scratch (digit totals, per-tile digit offsets) is this file-scope
 // array instead of stream-ordered allocations. It holds kNoAllocWords 32-bit
 // words (about 4 MB) on every device that loads the library, until exit.
 namespace {
 constexpr int64_t kNoAllocMaxRows = int64_t(1) << 21;
 constexpr int kNoAllocMaxTiles = (int)(kNoAllocMaxRows / kThreads);  // tiles hold >= 512 rows
-constexpr size_t kNoAllocHead = 320;                                  // histogram (256) + counter, padded
+constexpr size_t kNoAllocHead = 320;                                  // digit totals (256), padded
 constexpr size_t kNoAllocWords = kNoAllocHead + (size_t)kNoAllocMaxTiles * kRadixMax;
 __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 __device__ __align__(256) int g_noalloc_status[64];
@@ -558,9 +570,8 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
   a.shift = lo;
   a.width = width;
   a.transform = transform;
-  a.hist = scratch;
-  a.tile_counter = (int*)(scratch + 256);
-  a.status = scratch + kNoAllocHead;
+  a.offs = scratch + kNoAllocHead;
+  a.ld = (tiles + 3) & ~int64_t(3);
   a.err = ctx.d_status;
   a.tile_rows = tile_rows;
   a.chunks = chunks;
@@ -582,22 +593,18 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
   off += kWarps * kRadixMax * 2;
   cudaStream_t s = ctx.stream;
   gj_status st;
-  // the array keeps the previous call's contents: clear what must start at zero
-  if ((st = cuda_check(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * (kNoAllocHead + (size_t)tiles * kRadixMax), s))) !=
-      GJ_OK)
-    return st;
-  PassDigits pd{};
-  pd.passes = 1;
-  pd.shift[0] = lo;
-  pd.width[0] = width;
+  // the array keeps the previous call's contents: clear what must start at zero (the
+  // digit totals; every tile writes all of its offsets)
+  if ((st = cuda_check(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * kNoAllocHead, s))) != GJ_OK) return st;
   {
-    const int hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
     LaunchScope ls(ctx, KK_RADIX_HIST);
-    radix_hist_kernel<K><<<hist_blocks, 256, 0, s>>>((const K*)in->key, n, pd, transform, scratch);
+    const unsigned hb = (unsigned)std::min<int64_t>(tiles, (int64_t)ctx.num_sms * 8);
+    tile_hist_kernel<K><<<hb, kHistThreads, 0, s>>>((const K*)in->key, n, lo, width, transform, tile_rows, a.ld,
+                                                    scratch + kNoAllocHead, scratch);
   }
   {
     LaunchScope ls(ctx, KK_RADIX_HIST);
-    radix_bases_kernel<<<1, 256, 0, s>>>(scratch);
+    tile_offsets_kernel<<<1u << width, 1024, 0, s>>>(scratch + kNoAllocHead, scratch, a.ld);
   }
   if ((st = cuda_check(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSmemBudget + 16 * 1024))) != GJ_OK)
