@@ -214,8 +214,11 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t phase, int* er
 struct ColSet {
   const void* src[kMaxCols];
   void* dst[kMaxCols];
-  int32_t size[kMaxCols];  // bytes per element: 4 or 8
+  int32_t size[kMaxCols];  // bytes per element: 4, 8 or 16
   int32_t n;
+  // 1: the four 4-byte source columns are written interleaved, as one 16-byte
+  // column at dst[0] (row r's values at dst[0] + 16 r)
+  int32_t zip4;
 };
 
 __host__ __device__ __forceinline__ int dtype_size(int t) { return t == GJ_I64 ? 8 : 4; }

@@ -54,6 +54,10 @@ struct JoinIO {
   int64_t* d_count;
   int32_t stage_bulk;  // 1: probe keys 16-byte aligned, bulk-copied into shared memory
   int32_t narrow4;     // 1: every payload column 4 bytes wide, at most 4 per side
+  // GFTR with four 4-byte payloads on a side: that side's partitioned payloads as
+  // interleaved 16-byte rows (one load per row) instead of rsrc / ssrc
+  const int4* r_zip;
+  const int4* s_zip;
 };
 
 template <typename K>
@@ -503,8 +507,28 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
         const int32_t* __restrict__ ss = (const int32_t*)io.ssrc[q < io.ns_cols ? q : 0];
 #pragma unroll
         for (int j = 0; j < kEmitU; ++j) {
-          vr[q][j] = q < io.nr_cols ? __ldg(rs + (ok[j] ? ridx[j] : 0u)) : 0;
-          vs[q][j] = q < io.ns_cols ? __ldcs(ss + (ok[j] ? sidx[j] : 0u)) : 0;
+          vr[q][j] = (q < io.nr_cols && !io.r_zip) ? __ldg(rs + (ok[j] ? ridx[j] : 0u)) : 0;
+          vs[q][j] = (q < io.ns_cols && !io.s_zip) ? __ldcs(ss + (ok[j] ? sidx[j] : 0u)) : 0;
+        }
+      }
+      if (io.r_zip) {
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          const int4 v = __ldg(io.r_zip + (ok[j] ? ridx[j] : 0u));
+          vr[0][j] = v.x;
+          vr[1][j] = v.y;
+          vr[2][j] = v.z;
+          vr[3][j] = v.w;
+        }
+      }
+      if (io.s_zip) {
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          const int4 v = __ldcs(io.s_zip + (ok[j] ? sidx[j] : 0u));
+          vs[0][j] = v.x;
+          vs[1][j] = v.y;
+          vs[2][j] = v.z;
+          vs[3][j] = v.w;
         }
       }
 #pragma unroll
@@ -902,18 +926,31 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
     K* sk2 = scr.get_as<K>(ns);
     ColSet rc{}, sc{};
     if (gftr) {
+      // four 4-byte payloads on a side travel as one interleaved 16-byte row, read
+      // by the probe's path for sides of one to four 4-byte payloads
+      auto narrow = [](const gj_table* t) {
+        if (t->ncols < 1 || t->ncols > 4) return false;
+        for (int c = 0; c < t->ncols; ++c)
+          if (dtype_size(t->col_type[c]) != 4) return false;
+        return true;
+      };
+      const bool both_narrow = narrow(R) && narrow(S);
       rc.n = R->ncols;
+      rc.zip4 = both_narrow && R->ncols == 4 ? 1 : 0;
       for (int c = 0; c < R->ncols; ++c) {
         rc.src[c] = R->cols[c];
         rc.size[c] = dtype_size(R->col_type[c]);
-        rc.dst[c] = scr.get((size_t)std::max<int64_t>(nr, 1) * rc.size[c]);
+        if (!rc.zip4) rc.dst[c] = scr.get((size_t)std::max<int64_t>(nr, 1) * rc.size[c]);
       }
+      if (rc.zip4) rc.dst[0] = scr.get((size_t)std::max<int64_t>(nr, 1) * 16);
       sc.n = S->ncols;
+      sc.zip4 = both_narrow && S->ncols == 4 ? 1 : 0;
       for (int c = 0; c < S->ncols; ++c) {
         sc.src[c] = S->cols[c];
         sc.size[c] = dtype_size(S->col_type[c]);
-        sc.dst[c] = scr.get((size_t)ns * sc.size[c]);
+        if (!sc.zip4) sc.dst[c] = scr.get((size_t)ns * sc.size[c]);
       }
+      if (sc.zip4) sc.dst[0] = scr.get((size_t)ns * 16);
     } else {
       rc.n = sc.n = 1;
       rc.src[0] = sc.src[0] = nullptr;  // generated tuple ids
@@ -931,8 +968,12 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
     rk = rk2;
     sk = sk2;
     if (gftr) {
-      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = rc.dst[c];
-      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = sc.dst[c];
+      // zipped payloads are read through r_zip / s_zip; rsrc / ssrc keep a valid
+      // address for the unused column slots
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = rc.zip4 ? rc.dst[0] : rc.dst[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = sc.zip4 ? sc.dst[0] : sc.dst[c];
+      if (rc.zip4) io.r_zip = (const int4*)rc.dst[0];
+      if (sc.zip4) io.s_zip = (const int4*)sc.dst[0];
     } else {
       for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
       for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];

@@ -197,7 +197,27 @@ struct ScatterArgs {
   int bulk;       // 1: every source is 16-byte aligned, copy with cp.async.bulk
   int32_t col_off[kMaxCols];  // byte offset of each column's stage in shared memory (key at 0)
   int32_t inv_off, sdig_off, wcnt_off;
+  int4* zip_dst;  // non-null: the four 4-byte columns are written interleaved here instead
 };
+
+// Shared-memory layout for tiles of tile_rows rows: the key, every staged column,
+// the inverse index, the sorted digits and the per-warp digit counts. Returns the
+// dynamic shared-memory bytes.
+int scatter_layout(ScatterArgs& a, int tile_rows, int key_size, const ColSet& cols, uint32_t gen_mask) {
+  int off = tile_rows * key_size;
+  for (int c = 0; c < cols.n; ++c) {
+    a.col_off[c] = off;
+    if (!((gen_mask >> c) & 1u)) off += tile_rows * cols.size[c];
+  }
+  a.inv_off = off;
+  off += tile_rows * 2;
+  a.sdig_off = off;
+  off += tile_rows;
+  off = (off + 15) & ~15;
+  a.wcnt_off = off;
+  off += kWarps * kRadixMax * 2;
+  return off;
+}
 
 template <typename T>
 __device__ __forceinline__ void stage_tail(unsigned char* stage, const T* src, int64_t tile_base, int tile_n,
@@ -255,7 +275,9 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
       if ((a.gen_mask >> c) & 1u) continue;
       const int sz = a.cols.size[c];
       const int from = (int)((((uint32_t)tile_n * sz) & ~15u) / sz);
-      if (sz == 8)
+      if (sz == 16)
+        stage_tail<int4>(smem + a.col_off[c], (const int4*)a.cols.src[c], tile_base, tile_n, from);
+      else if (sz == 8)
         stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, from);
       else
         stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, from);
@@ -264,7 +286,9 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
     stage_tail<K>(smem, (const K*)a.kin, tile_base, tile_n, 0);
     for (int c = 0; c < a.cols.n; ++c) {
       if ((a.gen_mask >> c) & 1u) continue;
-      if (a.cols.size[c] == 8)
+      if (a.cols.size[c] == 16)
+        stage_tail<int4>(smem + a.col_off[c], (const int4*)a.cols.src[c], tile_base, tile_n, 0);
+      else if (a.cols.size[c] == 8)
         stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, 0);
       else
         stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, 0);
@@ -350,9 +374,33 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
     }
   }
   if (a.bulk) mbar_wait(&s_bar[1], 0, a.err);  // each thread observes the columns' arrival itself
+  if (a.zip_dst) {
+    // four 4-byte columns -> one 16-byte row each
+    const int32_t* st0 = (const int32_t*)(smem + a.col_off[0]);
+    const int32_t* st1 = (const int32_t*)(smem + a.col_off[1]);
+    const int32_t* st2 = (const int32_t*)(smem + a.col_off[2]);
+    const int32_t* st3 = (const int32_t*)(smem + a.col_off[3]);
+#pragma unroll
+    for (int i = 0; i < kMaxChunks; ++i) {
+      if (i >= a.chunks) break;
+      if (threadIdx.x + i * kThreads < tile_n) {
+        const int r = src_at[i];
+        a.zip_dst[dst_at[i]] = make_int4(st0[r], st1[r], st2[r], st3[r]);
+      }
+    }
+    return;
+  }
   for (int c = 0; c < a.cols.n; ++c) {
     const bool gen = (a.gen_mask >> c) & 1u;
-    if (a.cols.size[c] == 8) {
+    if (a.cols.size[c] == 16) {
+      const int4* st = (const int4*)(smem + a.col_off[c]);
+      int4* __restrict__ dst = (int4*)a.cols.dst[c];
+#pragma unroll
+      for (int i = 0; i < kMaxChunks; ++i) {
+        if (i >= a.chunks) break;
+        if (threadIdx.x + i * kThreads < tile_n) dst[dst_at[i]] = st[src_at[i]];
+      }
+    } else if (a.cols.size[c] == 8) {
       const int64_t* st = (const int64_t*)(smem + a.col_off[c]);
       int64_t* __restrict__ dst = (int64_t*)a.cols.dst[c];
 #pragma unroll
@@ -404,34 +452,23 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
 
-  ScatterArgs a{};
-  a.n = n;
-  a.transform = transform;
-  a.tile_rows = tile_rows;
-  a.chunks = chunks;
-  a.gen_mask = gen_mask;
-  int off = tile_rows * (int)sizeof(K);
-  for (int c = 0; c < cols_in.n; ++c) {
-    a.col_off[c] = off;
-    if (!((gen_mask >> c) & 1u)) off += tile_rows * cols_in.size[c];
+  // the columns every pass after the first reads and writes: with zip4 the
+  // interleaved 16-byte rows, else the input's columns
+  const bool zip = cols_in.zip4 != 0;
+  ColSet out_set = cols_in;
+  out_set.zip4 = 0;
+  if (zip) {
+    out_set.n = 1;
+    out_set.size[0] = 16;
   }
-  a.inv_off = off;
-  off += tile_rows * 2;
-  a.sdig_off = off;
-  off += tile_rows;
-  off = (off + 15) & ~15;
-  a.wcnt_off = off;
-  off += kWarps * kRadixMax * 2;
-  const size_t dyn = (size_t)off;
-
+  ColSet tmp = out_set;
+  K* ktmp = nullptr;
   uint32_t* total = scr.get_as<uint32_t>((size_t)plan.passes * kRadixMax);
   const int64_t ld = (tiles + 3) & ~int64_t(3);                      // row stride of the tile offsets
   uint32_t* offs = scr.get_as<uint32_t>((size_t)ld * kRadixMax);     // reused by every pass
-  K* ktmp = nullptr;
-  ColSet tmp = cols_in;
   if (plan.passes > 1) {
     ktmp = scr.get_as<K>(n);
-    for (int c = 0; c < cols_in.n; ++c) tmp.dst[c] = scr.get((size_t)n * cols_in.size[c]);
+    for (int c = 0; c < out_set.n; ++c) tmp.dst[c] = scr.get((size_t)n * out_set.size[c]);
   }
   if (scr.failed()) return GJ_ERR_OOM;
   cudaStream_t s = ctx.stream;
@@ -444,16 +481,31 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   }
   for (int q = 0; q < plan.passes; ++q) {
     const bool to_out = ((plan.passes - 1 - q) % 2) == 0;
+    ScatterArgs a{};
+    a.n = n;
+    a.transform = transform;
+    a.tile_rows = tile_rows;
+    a.chunks = chunks;
     a.kin = q == 0 ? (const void*)kin : (to_out ? (const void*)ktmp : (const void*)kout);
     a.kout = to_out ? (void*)kout : (void*)ktmp;
-    a.cols = cols_in;
-    bool bulk = aligned16(a.kin);
-    for (int c = 0; c < cols_in.n; ++c) {
-      const void* prev_dst = to_out ? tmp.dst[c] : cols_in.dst[c];  // where the previous pass wrote
-      a.cols.src[c] = q == 0 ? cols_in.src[c] : prev_dst;
-      a.cols.dst[c] = to_out ? cols_in.dst[c] : tmp.dst[c];
-      if (a.cols.src[c] && !aligned16(a.cols.src[c])) bulk = false;
+    const ColSet& dst_set = to_out ? out_set : tmp;
+    const ColSet& prev_set = to_out ? tmp : out_set;  // where the previous pass wrote
+    if (q == 0) {
+      a.cols = cols_in;
+      if (zip)
+        a.zip_dst = (int4*)dst_set.dst[0];
+      else
+        for (int c = 0; c < cols_in.n; ++c) a.cols.dst[c] = dst_set.dst[c];
+    } else {
+      a.cols = out_set;
+      for (int c = 0; c < out_set.n; ++c) {
+        a.cols.src[c] = prev_set.dst[c];
+        a.cols.dst[c] = dst_set.dst[c];
+      }
     }
+    bool bulk = aligned16(a.kin);
+    for (int c = 0; c < a.cols.n; ++c)
+      if (a.cols.src[c] && !aligned16(a.cols.src[c])) bulk = false;
     a.gen_mask = q == 0 ? gen_mask : 0u;
     a.bulk = bulk ? 1 : 0;
     a.shift = plan.shift[q];
@@ -461,6 +513,8 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     a.offs = offs;
     a.ld = ld;
     a.err = ctx.d_status;
+    // tuple ids are generated in the first pass and staged like any column after it
+    const size_t dyn = (size_t)scatter_layout(a, tile_rows, (int)sizeof(K), a.cols, a.gen_mask);
     {
       // where each tile's rows of each digit go: tile histograms, then their scan
       LaunchScope ls(ctx, KK_RADIX_HIST);
@@ -471,24 +525,6 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     {
       LaunchScope ls(ctx, KK_RADIX_HIST);
       tile_offsets_kernel<<<1u << a.width, 1024, 0, s>>>(offs, total + q * kRadixMax, ld);
-    }
-    if (q > 0 && gen_mask) {
-      // tuple ids now sit in shared memory like any other column
-      int o = tile_rows * (int)sizeof(K);
-      for (int c = 0; c < cols_in.n; ++c) {
-        a.col_off[c] = o;
-        o += tile_rows * cols_in.size[c];
-      }
-      a.inv_off = o;
-      o += tile_rows * 2;
-      a.sdig_off = o;
-      o += tile_rows;
-      o = (o + 15) & ~15;
-      a.wcnt_off = o;
-      o += kWarps * kRadixMax * 2;
-      LaunchScope ls(ctx, KK_RADIX_SCATTER);
-      radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, (size_t)o, s>>>(a);
-      continue;
     }
     LaunchScope ls(ctx, KK_RADIX_SCATTER);
     radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, dyn, s>>>(a);
@@ -579,18 +615,7 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
   for (int c = 0; c < cols.n; ++c)
     if (!aligned16(cols.src[c])) bulk = false;
   a.bulk = bulk ? 1 : 0;
-  int off = tile_rows * (int)sizeof(K);
-  for (int c = 0; c < cols.n; ++c) {
-    a.col_off[c] = off;
-    off += tile_rows * cols.size[c];
-  }
-  a.inv_off = off;
-  off += tile_rows * 2;
-  a.sdig_off = off;
-  off += tile_rows;
-  off = (off + 15) & ~15;
-  a.wcnt_off = off;
-  off += kWarps * kRadixMax * 2;
+  const int off = scatter_layout(a, tile_rows, (int)sizeof(K), cols, 0u);
   cudaStream_t s = ctx.stream;
   gj_status st;
   // the array keeps the previous call's contents: clear what must start at zero (the
