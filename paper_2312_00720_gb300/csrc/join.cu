@@ -289,6 +289,7 @@ __device__ void probe_tile(const K* __restrict__ rkey, const int64_t* __restrict
 // of a group of columns in flight before its stores.
 constexpr int kUnitSub = 2;                   // sub-tiles per unit
 constexpr int kUnitRows = kUnitSub * kTileS;  // probe rows per unit
+constexpr int kRoffCache = 64;              // partition bounds cached per unit
 constexpr int kEmitU = 4;                     // rows per lane per emit step
 
 template <typename K>
@@ -336,6 +337,9 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
   __shared__ int64_t s_unit;
   __shared__ uint32_t s_wcnt[kThreads / 32];
   __shared__ uint64_t s_base;
+  __shared__ int64_t s_roff[kRoffCache];  // roff[s_p0 .. s_p0 + s_nroff) of the unit's partitions
+  __shared__ uint32_t s_p0;
+  __shared__ int s_nroff;
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) {
@@ -363,6 +367,25 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
     mbar_expect_tx(&s_bar[0], kb);
     if (kb) bulk_g2s(s_kbuf, skey + u0, kb, &s_bar[0]);
   }
+  // while the keys arrive, one warp fetches the partition bounds the unit needs:
+  // its rows are sorted by partition, so they lie between those of its first and
+  // last row
+  if (warp == 0) {
+    uint32_t p0 = 0, p1 = 0;
+    if (lane == 0) {
+      const K kf = skey[u0], kl = skey[u0 + un - 1];
+      p0 = (uint32_t)KeyTraits<K>::hash64(kf) & pmask;
+      p1 = (uint32_t)KeyTraits<K>::hash64(kl) & pmask;
+    }
+    p0 = __shfl_sync(0xffffffffu, p0, 0);
+    p1 = __shfl_sync(0xffffffffu, p1, 0);
+    const int nr = min((int)(p1 - p0) + 2, kRoffCache);
+    for (int e = lane; e < nr; e += 32) s_roff[e] = roff[p0 + e];
+    if (lane == 0) {
+      s_p0 = p0;
+      s_nroff = nr;
+    }
+  }
   int64_t cur_p = -1;  // partition whose whole build side is in the table
   for (int k = 0; k < nsub; ++k) {
     const int rows = min(kTileS, un - k * kTileS);
@@ -379,8 +402,6 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
     for (int i = body_rows(k) + t; i < rows; i += kThreads) kb[i] = skey[sbase + i];
     mbar_wait(&s_bar[k & 1], (uint32_t)((k >> 1) & 1), err);
     __syncthreads();
-    for (int i = t; i < rows; i += kThreads) mid[i] = -1;
-    __syncthreads();
     // the partitions present in the sub-tile (non-decreasing in S')
     auto part_of = [&](int i) { return (uint32_t)KeyTraits<K>::hash64(kb[i]) & pmask; };
     int a = 0;
@@ -392,7 +413,12 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
         if (part_of(m) <= p) lo = m + 1; else hi = m;
       }
       const int b = lo;
-      const int64_t r_lo = roff[p], r_hi = roff[p + 1];
+      const int e = (int)(p - s_p0);  // the unit's partitions come from its bound cache
+      const int64_t r_lo = e + 1 < s_nroff ? s_roff[e] : roff[p];
+      const int64_t r_hi = e + 1 < s_nroff ? s_roff[e + 1] : roff[p + 1];
+      // rows of a partition without build rows match nothing
+      if (r_hi == r_lo)
+        for (int i = a + t; i < b; i += kThreads) mid[i] = -1;
       const bool whole = r_hi - r_lo <= kBuildCap;
       for (int64_t c0 = r_lo; c0 < r_hi; c0 += kBuildCap) {
         const int cn = (int)min64(kBuildCap, r_hi - c0);
@@ -416,18 +442,27 @@ __global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restri
           }
           __syncthreads();
         }
+        // the first chunk decides every row (match or -1); later chunks of a large
+        // partition only add matches
+        const bool first_chunk = c0 == r_lo;
         for (int i = a + t; i < b; i += kThreads) {
           const K kk = kb[i];
           uint32_t sl = smem_slot<K>(kk, pbits);
+          int32_t m = -1;
           for (int probe = 0; probe < kSlots; ++probe) {
             const int v = s_slots[sl];
             if (v == 0) break;
             if (s_rkey[v - 1] == kk) {
-              if (mid[i] >= 0) set_status(err, GJ_ERR_DUPLICATE_KEY);
-              mid[i] = (int32_t)(c0 + v - 1);
+              m = (int32_t)(c0 + v - 1);
               break;
             }
             sl = (sl + 1) & (kSlots - 1);
+          }
+          if (first_chunk) {
+            mid[i] = m;
+          } else if (m >= 0) {
+            if (mid[i] >= 0) set_status(err, GJ_ERR_DUPLICATE_KEY);
+            mid[i] = m;
           }
         }
         __syncthreads();  // the table may be rebuilt next
