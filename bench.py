@@ -325,10 +325,11 @@ def main():
     prof = gj.profile_read()
     gj.profile_enable(False)
     alg_bytes_per_step = {
-        # two 8-bit passes over R and over S, each reading and writing key + payloads
+        # two passes (8 + 7 bits) over R and over S, each reading and writing key + payloads
         "radix_scatter": 2 * 2 * (NR + NS) * ROW_BYTES,
-        # one read of every key for the histograms of both passes
-        "radix_hist": 4 * (NR + NS),
+        # per pass, one read of every key for the tile histograms (the per-digit
+        # scans of the tile counts are not counted)
+        "radix_hist": 2 * 4 * (NR + NS),
         # read S' and R' once, write T
         "phj_probe": (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES,
         "partition_bounds": 4 * NR,

@@ -196,7 +196,7 @@ struct ScatterArgs {
   int chunks;     // 32-row chunks per warp
   int bulk;       // 1: every source is 16-byte aligned, copy with cp.async.bulk
   int32_t col_off[kMaxCols];  // byte offset of each column's stage in shared memory (key at 0)
-  int32_t inv_off, sdig_off, wcnt_off;
+  int32_t perm_off, wcnt_off;
   int4* zip_dst;  // non-null: the four 4-byte columns are written interleaved here instead
 };
 
@@ -209,11 +209,9 @@ int scatter_layout(ScatterArgs& a, int tile_rows, int key_size, const ColSet& co
     a.col_off[c] = off;
     if (!((gen_mask >> c) & 1u)) off += tile_rows * cols.size[c];
   }
-  a.inv_off = off;
-  off += tile_rows * 2;
-  a.sdig_off = off;
-  off += tile_rows;
   off = (off + 15) & ~15;
+  a.perm_off = off;
+  off += tile_rows * 4;
   a.wcnt_off = off;
   off += kWarps * kRadixMax * 2;
   return off;
@@ -229,7 +227,7 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint32_t s_tstart[kRadixMax];
-  __shared__ int64_t s_gdst[kRadixMax];
+  __shared__ int32_t s_gdst[kRadixMax];  // output position of sorted position 0 of each digit
   __shared__ uint32_t s_scan[kWarps];
   __shared__ __align__(8) uint64_t s_bar[2];
 
@@ -237,8 +235,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1;
   K* s_key = (K*)smem;
-  uint16_t* s_inv = (uint16_t*)(smem + a.inv_off);
-  uint8_t* s_sdig = smem + a.sdig_off;
+  uint32_t* s_perm = (uint32_t*)(smem + a.perm_off);  // sorted position -> digit << 16 | row of the tile
   uint16_t* s_wcnt = (uint16_t*)(smem + a.wcnt_off);  // [kWarps][kRadixMax]
 
   if (threadIdx.x == 0) {
@@ -334,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   const uint32_t tstart = block_excl_scan(tcnt, s_scan);
   if (d < radix) {
     s_tstart[d] = tstart;
-    s_gdst[d] = (int64_t)a.offs[(int64_t)d * a.ld + tile] - tstart;
+    s_gdst[d] = (int32_t)(a.offs[(int64_t)d * a.ld + tile] - tstart);  // rows < 2^31
   }
   __syncthreads();
 
@@ -345,8 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
     const int row = seg + i * 32 + lane;
     if (row < tile_n) {
       const uint32_t p = s_tstart[dg[i]] + s_wcnt[warp * kRadixMax + dg[i]] + rank[i];
-      s_inv[p] = (uint16_t)row;
-      s_sdig[p] = dg[i];
+      s_perm[p] = (uint32_t)dg[i] << 16 | (uint32_t)row;
     }
   }
   __syncthreads();
@@ -361,8 +357,9 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
     if (i >= a.chunks) break;
     const int p = threadIdx.x + i * kThreads;
     if (p < tile_n) {
-      dst_at[i] = (uint32_t)(s_gdst[s_sdig[p]] + p);
-      src_at[i] = s_inv[p];
+      const uint32_t e = s_perm[p];
+      dst_at[i] = (uint32_t)(s_gdst[e >> 16] + p);
+      src_at[i] = (uint16_t)(e & 0xffffu);
     }
   }
   {
@@ -446,8 +443,8 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     if (cols_in.src[c] == nullptr) gen_mask |= 1u << c;
     row_bytes += cols_in.size[c];
   }
-  // tile: 512 rows per chunk step; staged bytes + 3 bytes/row of indices within the budget
-  int chunks = kSmemBudget / (kThreads * (row_bytes + 3));
+  // tile: 512 rows per chunk step; staged bytes + 4 bytes/row of permutation within the budget
+  int chunks = kSmemBudget / (kThreads * (row_bytes + 4));
   chunks = std::max(1, std::min(kMaxChunks, chunks));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
@@ -595,7 +592,7 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
     cols.size[c] = dtype_size(in->col_type[c]);
     row_bytes += cols.size[c];
   }
-  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * (row_bytes + 3))));
+  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * (row_bytes + 4))));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
   ScatterArgs a{};
