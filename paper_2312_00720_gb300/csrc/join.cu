@@ -33,7 +33,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTileS = 2048;          // probe rows per tile
 constexpr int kItems = kTileS / kThreads;
-constexpr int kBuildCap = 2048;       // build rows per shared-memory table
+constexpr int kBuildCap = 1024;       // build rows per shared-memory table
 constexpr int kSlots = 2 * kBuildCap; // load factor <= 1/2
 
 struct JoinIO {
@@ -323,7 +323,7 @@ __device__ __forceinline__ void emit_cols(const JoinIO& io, int c, int g, bool r
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 3) phj_unit_kernel(const K* __restrict__ rkey,
+__global__ void __launch_bounds__(kThreads, 4) phj_unit_kernel(const K* __restrict__ rkey,
                                                             const int64_t* __restrict__ roff, int pbits,
                                                             const K* __restrict__ skey, int64_t ns, JoinIO io,
                                                             uint64_t* unit_status, int* unit_counter, int64_t nunits,
@@ -1225,7 +1225,7 @@ gj_status join_groupby_run(const Ctx& ctx, const gj_table* R, const gj_table* S,
   // a global table on a build side of a few million rows stays in L2; larger
   // build sides are partitioned
   if (variant == GJ_JOIN_AUTO) variant = R->n <= (int64_t(1) << 22) ? GJ_JOIN_NPHJ : GJ_JOIN_PHJ_TR;
-  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 1024);
+  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 512);
   if (R->key_type == GJ_I64)
     return join_groupby_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, gk, nagg, ops, agg_cols, opt,
                                        out_keys, out_aggs, cap, d_ngroups);
@@ -1254,7 +1254,7 @@ gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const g
   int variant = opt->join_variant;
   if (variant == GJ_JOIN_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(R, S, 0, opt, true);
   if (variant == GJ_JOIN_AUTO) variant = heuristic_join_variant(R, opt);
-  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 1024);
+  int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 512);
   if (R->key_type == GJ_I64)
     return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
   return join_typed<int32_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
