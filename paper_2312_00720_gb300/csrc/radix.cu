@@ -33,7 +33,7 @@ constexpr int kHistThreads = 256;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChunks = 8;  // 32-row chunks per warp: tiles of up to 4096 rows
-constexpr int kSmemBudget = 100 * 1024;  // in-stage + per-row arrays; two blocks per SM
+constexpr int kSmemBudget = 48 * 1024;  // staged key + per-row arrays; three blocks per SM
 
 
 // Exclusive scan of one value per thread over the block.
@@ -195,26 +195,25 @@ struct ScatterArgs {
   int tile_rows;  // 512 * chunks
   int chunks;     // 32-row chunks per warp
   int bulk;       // 1: every source is 16-byte aligned, copy with cp.async.bulk
-  int32_t col_off[kMaxCols];  // byte offset of each column's stage in shared memory (key at 0)
   int32_t perm_off, wcnt_off;
   int4* zip_dst;  // non-null: the four 4-byte columns are written interleaved here instead
 };
 
-// Shared-memory layout for tiles of tile_rows rows: the key, every staged column,
-// the inverse index, the sorted digits and the per-warp digit counts. Returns the
-// dynamic shared-memory bytes.
-int scatter_layout(ScatterArgs& a, int tile_rows, int key_size, const ColSet& cols, uint32_t gen_mask) {
+// Shared-memory layout for tiles of tile_rows rows: the staged key, the
+// permutation words and the per-warp digit counts. Returns the dynamic
+// shared-memory bytes.
+int scatter_layout(ScatterArgs& a, int tile_rows, int key_size) {
   int off = tile_rows * key_size;
-  for (int c = 0; c < cols.n; ++c) {
-    a.col_off[c] = off;
-    if (!((gen_mask >> c) & 1u)) off += tile_rows * cols.size[c];
-  }
   off = (off + 15) & ~15;
   a.perm_off = off;
   off += tile_rows * 4;
   a.wcnt_off = off;
   off += kWarps * kRadixMax * 2;
   return off;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <typename T>
@@ -224,12 +223,12 @@ __device__ __forceinline__ void stage_tail(unsigned char* stage, const T* src, i
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) radix_scatter_kernel(ScatterArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint32_t s_tstart[kRadixMax];
   __shared__ int32_t s_gdst[kRadixMax];  // output position of sorted position 0 of each digit
   __shared__ uint32_t s_scan[kWarps];
-  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ __align__(8) uint64_t s_bar[1];
 
   const int radix = 1 << a.width;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -240,7 +239,6 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
 
   if (threadIdx.x == 0) {
     mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -248,48 +246,23 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   const int64_t tile_base = (int64_t)tile * a.tile_rows;
   const int tile_n = (int)min64(a.tile_rows, a.n - tile_base);
 
-  // ---- stage the tile: key first (ranking needs only it), then the columns
+  // ---- stage the tile's key in shared memory (ranking needs only it); the columns
+  // are prefetched into L2 and gathered from there in digit order, which keeps
+  // shared memory small enough for three blocks per SM
   if (a.bulk) {
     if (threadIdx.x == 0) {
       uint32_t kb = ((uint32_t)tile_n * sizeof(K)) & ~15u;
       mbar_expect_tx(&s_bar[0], kb);
       if (kb) bulk_g2s(s_key, (const K*)a.kin + tile_base, kb, &s_bar[0]);
-      uint32_t cb = 0;
-      for (int c = 0; c < a.cols.n; ++c)
-        if (!((a.gen_mask >> c) & 1u)) cb += ((uint32_t)tile_n * a.cols.size[c]) & ~15u;
-      mbar_expect_tx(&s_bar[1], cb);
       for (int c = 0; c < a.cols.n; ++c) {
         if ((a.gen_mask >> c) & 1u) continue;
         uint32_t b = ((uint32_t)tile_n * a.cols.size[c]) & ~15u;
-        if (b)
-          bulk_g2s(smem + a.col_off[c], (const unsigned char*)a.cols.src[c] + tile_base * a.cols.size[c], b,
-                   &s_bar[1]);
+        if (b) prefetch_l2((const unsigned char*)a.cols.src[c] + tile_base * a.cols.size[c], b);
       }
     }
-    // the last few elements of a ragged tile with plain loads
     stage_tail<K>(smem, (const K*)a.kin, tile_base, tile_n, (int)((((uint32_t)tile_n * sizeof(K)) & ~15u) / sizeof(K)));
-    for (int c = 0; c < a.cols.n; ++c) {
-      if ((a.gen_mask >> c) & 1u) continue;
-      const int sz = a.cols.size[c];
-      const int from = (int)((((uint32_t)tile_n * sz) & ~15u) / sz);
-      if (sz == 16)
-        stage_tail<int4>(smem + a.col_off[c], (const int4*)a.cols.src[c], tile_base, tile_n, from);
-      else if (sz == 8)
-        stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, from);
-      else
-        stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, from);
-    }
   } else {
     stage_tail<K>(smem, (const K*)a.kin, tile_base, tile_n, 0);
-    for (int c = 0; c < a.cols.n; ++c) {
-      if ((a.gen_mask >> c) & 1u) continue;
-      if (a.cols.size[c] == 16)
-        stage_tail<int4>(smem + a.col_off[c], (const int4*)a.cols.src[c], tile_base, tile_n, 0);
-      else if (a.cols.size[c] == 8)
-        stage_tail<int64_t>(smem + a.col_off[c], (const int64_t*)a.cols.src[c], tile_base, tile_n, 0);
-      else
-        stage_tail<int32_t>(smem + a.col_off[c], (const int32_t*)a.cols.src[c], tile_base, tile_n, 0);
-    }
   }
   for (int i = threadIdx.x; i < kWarps * kRadixMax; i += kThreads) s_wcnt[i] = 0;
   if (a.bulk) mbar_wait(&s_bar[0], 0, a.err);
@@ -370,13 +343,12 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
       if (threadIdx.x + i * kThreads < tile_n) kout[dst_at[i]] = s_key[src_at[i]];
     }
   }
-  if (a.bulk) mbar_wait(&s_bar[1], 0, a.err);  // each thread observes the columns' arrival itself
   if (a.zip_dst) {
     // four 4-byte columns -> one 16-byte row each
-    const int32_t* st0 = (const int32_t*)(smem + a.col_off[0]);
-    const int32_t* st1 = (const int32_t*)(smem + a.col_off[1]);
-    const int32_t* st2 = (const int32_t*)(smem + a.col_off[2]);
-    const int32_t* st3 = (const int32_t*)(smem + a.col_off[3]);
+    const int32_t* st0 = (const int32_t*)a.cols.src[0] + tile_base;
+    const int32_t* st1 = (const int32_t*)a.cols.src[1] + tile_base;
+    const int32_t* st2 = (const int32_t*)a.cols.src[2] + tile_base;
+    const int32_t* st3 = (const int32_t*)a.cols.src[3] + tile_base;
 #pragma unroll
     for (int i = 0; i < kMaxChunks; ++i) {
       if (i >= a.chunks) break;
@@ -390,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
   for (int c = 0; c < a.cols.n; ++c) {
     const bool gen = (a.gen_mask >> c) & 1u;
     if (a.cols.size[c] == 16) {
-      const int4* st = (const int4*)(smem + a.col_off[c]);
+      const int4* st = (const int4*)a.cols.src[c] + tile_base;
       int4* __restrict__ dst = (int4*)a.cols.dst[c];
 #pragma unroll
       for (int i = 0; i < kMaxChunks; ++i) {
@@ -398,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
         if (threadIdx.x + i * kThreads < tile_n) dst[dst_at[i]] = st[src_at[i]];
       }
     } else if (a.cols.size[c] == 8) {
-      const int64_t* st = (const int64_t*)(smem + a.col_off[c]);
+      const int64_t* st = gen ? nullptr : (const int64_t*)a.cols.src[c] + tile_base;
       int64_t* __restrict__ dst = (int64_t*)a.cols.dst[c];
 #pragma unroll
       for (int i = 0; i < kMaxChunks; ++i) {
@@ -406,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 2) radix_scatter_kernel(ScatterArgs 
         if (threadIdx.x + i * kThreads < tile_n) dst[dst_at[i]] = gen ? tile_base + src_at[i] : st[src_at[i]];
       }
     } else {
-      const int32_t* st = (const int32_t*)(smem + a.col_off[c]);
+      const int32_t* st = gen ? nullptr : (const int32_t*)a.cols.src[c] + tile_base;
       int32_t* __restrict__ dst = (int32_t*)a.cols.dst[c];
 #pragma unroll
       for (int i = 0; i < kMaxChunks; ++i) {
@@ -438,13 +410,10 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   RadixPlan plan = make_radix_plan(lo, hi, bits_per_pass);
   if (n == 0) return GJ_OK;
   uint32_t gen_mask = 0;
-  int row_bytes = sizeof(K);  // generated tuple ids are staged from the second pass on: count them
-  for (int c = 0; c < cols_in.n; ++c) {
+  for (int c = 0; c < cols_in.n; ++c)
     if (cols_in.src[c] == nullptr) gen_mask |= 1u << c;
-    row_bytes += cols_in.size[c];
-  }
-  // tile: 512 rows per chunk step; staged bytes + 4 bytes/row of permutation within the budget
-  int chunks = kSmemBudget / (kThreads * (row_bytes + 4));
+  // tile: 512 rows per chunk step; staged key + 4 bytes/row of permutation within the budget
+  int chunks = kSmemBudget / (kThreads * ((int)sizeof(K) + 4));
   chunks = std::max(1, std::min(kMaxChunks, chunks));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
@@ -511,7 +480,7 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
     a.ld = ld;
     a.err = ctx.d_status;
     // tuple ids are generated in the first pass and staged like any column after it
-    const size_t dyn = (size_t)scatter_layout(a, tile_rows, (int)sizeof(K), a.cols, a.gen_mask);
+    const size_t dyn = (size_t)scatter_layout(a, tile_rows, (int)sizeof(K));
     {
       // where each tile's rows of each digit go: tile histograms, then their scan
       LaunchScope ls(ctx, KK_RADIX_HIST);
@@ -585,14 +554,12 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
   const int width = hi - lo;
   ColSet cols{};
   cols.n = in->ncols;
-  int row_bytes = sizeof(K);
   for (int c = 0; c < in->ncols; ++c) {
     cols.src[c] = in->cols[c];
     cols.dst[c] = out->cols[c];
     cols.size[c] = dtype_size(in->col_type[c]);
-    row_bytes += cols.size[c];
   }
-  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * (row_bytes + 4))));
+  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * ((int)sizeof(K) + 4))));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
   ScatterArgs a{};
@@ -612,7 +579,7 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
   for (int c = 0; c < cols.n; ++c)
     if (!aligned16(cols.src[c])) bulk = false;
   a.bulk = bulk ? 1 : 0;
-  const int off = scatter_layout(a, tile_rows, (int)sizeof(K), cols, 0u);
+  const int off = scatter_layout(a, tile_rows, (int)sizeof(K));
   cudaStream_t s = ctx.stream;
   gj_status st;
   // the array keeps the previous call's contents: clear what must start at zero (the
