@@ -849,16 +849,22 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
   constexpr int kOneGroupAggs = 8;
   const bool one_group = q == 0 && total == 1;
 
-  // ---- few groups, one round: every aggregate in one pass over the partition
+  // ---- few groups, one round: every aggregate in one pass over the partition.
+  // When the slots are few, every warp updates its own copy (no contention
+  // between warps) and the copies are combined at the end.
   if (q == 0 && !one_group && total * A.n <= kPgbCap) {
     const int g = (int)total;
+    const int nsl = g * A.n;
+    constexpr int kWarpsPgb = kPgbThreads / 32;
+    const int ncopy = nsl * kWarpsPgb <= kPgbCap ? kWarpsPgb : 1;
+    int64_t* my = s_agg + (ncopy > 1 ? (threadIdx.x >> 5) * nsl : 0);
     for (int l = threadIdx.x; l < g; l += blockDim.x) {
       if (goff + l < cap)
         out_keys[goff + l] = s_keys[l];
       else
         set_status(err, GJ_ERR_CAPACITY);
     }
-    for (int s = threadIdx.x; s < g * A.n; s += blockDim.x) s_agg[s] = agg_identity(A.op[s / g]);
+    for (int s = threadIdx.x; s < nsl * ncopy; s += blockDim.x) s_agg[s] = agg_identity(A.op[(s % nsl) / g]);
     __syncthreads();
     constexpr int kBatch = 4;
     for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
@@ -882,13 +888,15 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
       for (int j = 0; j < A.n; ++j) {
 #pragma unroll
         for (int u = 0; u < kBatch; ++u)
-          if (lid[u] >= 0) agg_atomic(A.op[j], &s_agg[j * g + lid[u]], cached_value<kBatch>(A, cc, j, cv, u, row[u]));
+          if (lid[u] >= 0) agg_atomic(A.op[j], &my[j * g + lid[u]], cached_value<kBatch>(A, cc, j, cv, u, row[u]));
       }
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < g * A.n; s += blockDim.x) {
+    for (int s = threadIdx.x; s < nsl; s += blockDim.x) {
       const int j = s / g, l = s - j * g;
-      if (goff + l < cap) A.out[j][goff + l] = s_agg[s];
+      int64_t v = s_agg[s];
+      for (int c = 1; c < ncopy; ++c) v = agg_combine(A.op[j], v, s_agg[c * nsl + s]);
+      if (goff + l < cap) A.out[j][goff + l] = v;
     }
     return;
   }
