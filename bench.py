@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NR, NS, NCOLS = 1 << 25, 1 << 27, 4
+METRIC = "join input tuples/s ((|R|+|S|)/time), plain FK-PK join at scale"
 ROW_BYTES = 4 + 4 * NCOLS              # key + payloads of one input row
 OUT_ROW_BYTES = 4 + 4 * 2 * NCOLS      # T(key, r1..r4, s1..s4)
 MIN_BYTES = (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES
@@ -133,7 +134,19 @@ def _event_ms(fn, steps: int) -> float:
     return a.elapsed_time(b) / steps
 
 
-def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20):
+def oracle_sample(fn, rows: int, what: str):
+    """Times one call of an oracle function (single-threaded, this process) on a
+    bounded sample; returns the cpu_baseline object of a line."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    fn(oracle)
+    dt = time.perf_counter() - t0
+    return {"value": rows / dt / 1e9, "unit": "Gtuples/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what}, {dt:.1f} s"}
+
+
+def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20, cpu: bool = True):
     """Plain grouped aggregation: 2^27 rows, int32 keys from 2^log2_groups ids,
     3 int32 value columns, COUNT + SUM/MIN/MAX per column (10 int64 aggregates)."""
     import torch
@@ -154,10 +167,15 @@ def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20):
         out[v] = {"ms": ms, "gtuples_s": n / (ms * 1e-3) / 1e9,
                   "min_bytes_frac": min_bytes / (ms * 1e-3) / 1e9 / peak}
     del key, vals
+    if cpu:
+        m = 1 << 24  # the first 2^24 rows of the same input
+        out["cpu_baseline"] = oracle_sample(
+            lambda o: o.groupby_hash(w["key"][:m], [c[:m] for c in w["vals"]], aggs, cols), m,
+            "first 2^24 rows of the same input, std::unordered_map group-by, 10 aggregates")
     return out
 
 
-def bench_one_query(gj, wl, steps: int = 20):
+def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True):
     """One query: |R| = 2^20 ⋈ |S| = 2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay), not materialised."""
     import torch
     w = wl.join_groupby_workload()
@@ -170,10 +188,15 @@ def bench_one_query(gj, wl, steps: int = 20):
         assert int(outs[1][: int(ng.item())].sum().item()) == 1 << 22
         ms = _event_ms(lambda: gj.join_groupby(*args, variant=v, sync=False), steps)
         out[v] = {"us": ms * 1e3, "gtuples_s": ((1 << 20) + (1 << 22)) / (ms * 1e-3) / 1e9}
+    if cpu:
+        out["cpu_baseline"] = oracle_sample(
+            lambda o: o.join_groupby(w["rkey"], w["rcols"], w["skey"], w["scols"], g_side=0, g_col=0, g_mod=1024,
+                                     aggs=["sum", "count"], agg_side=[1, 1], agg_col=[0, 0]),
+            (1 << 20) + (1 << 22), "the whole query, std::unordered_map join then group-by")
     return out
 
 
-def bench_batch(gj, wl, steps: int = 5):
+def bench_batch(gj, wl, steps: int = 5, cpu: bool = True):
     """512 join + group-by instances: one persistent graph launch vs 512 sequential gj_join_groupby calls."""
     import torch
     ws = wl.batch_workload(512, seed=7)
@@ -198,7 +221,16 @@ def bench_batch(gj, wl, steps: int = 5):
     rows = sum(len(w["rkey"]) + len(w["skey"]) for w in ws)
     cfg = plan.config()
     plan.close()
-    return {"workload": "512 instances, |R| log-uniform [2^10, 2^20], |S| = 4|R|, 2 int32 payloads per side, "
+    out = {}
+    if cpu:
+        sub = ws[:64]  # the first 64 instances
+        out["cpu_baseline"] = oracle_sample(
+            lambda o: [o.join_groupby(w["rkey"], w["rcols"], w["skey"], w["scols"], g_side=0, g_col=0,
+                                      g_mod=w["modulus"], aggs=aggs, agg_side=[1, 1, 1, 0], agg_col=[0, 0, 1, 1])
+                       for w in sub],
+            sum(len(w["rkey"]) + len(w["skey"]) for w in sub),
+            "the first 64 of the 512 instances, std::unordered_map join then group-by each")
+    return {**out, "workload": "512 instances, |R| log-uniform [2^10, 2^20], |S| = 4|R|, 2 int32 payloads per side, "
                         "GROUP BY R.p0 mod G (G log-uniform [2^2, 2^16]), COUNT, SUM(S.p0), SUM(S.p1), SUM(R.p1)",
             "rows": rows, "batched_ms": batched, "sequential_ms": seq, "speedup": seq / batched,
             "batched_gtuples_s": rows / (batched * 1e-3) / 1e9, "sequential_gtuples_s": rows / (seq * 1e-3) / 1e9,
@@ -223,7 +255,12 @@ def run_reference(args, world, rank):
     import oracle
     from paper_2312_00720_gb300 import workloads as wl
 
+    # each step joins a sample small enough that all steps end within about two and
+    # a half minutes (the oracle runs at roughly 1.5 M tuples/s on one core)
+    budget_rows = 150.0 / max(1, args.steps) * 1.5e6
     shift = 3
+    while shift < 12 and (NR + NS) >> shift > budget_rows:
+        shift += 1
     nr, ns = NR >> shift, NS >> shift
     w = wl.join_workload(nr, ns, NCOLS, NCOLS, seed=SEED)
     oracle.build()
@@ -238,7 +275,7 @@ def run_reference(args, world, rank):
     dt = sum(times)
     value = args.steps * (nr + ns) / dt / 1e9
     print(json.dumps({
-        "impl": "reference", "metric": "join input tuples/s ((|R|+|S|)/time)", "value": value,
+        "impl": "reference", "metric": METRIC, "value": value,
         "unit": "Gtuples/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -379,7 +416,7 @@ def main():
 
     if rank == 0:
         out = {
-            "metric": "join input tuples/s ((|R|+|S|)/time), plain FK-PK join at scale",
+            "metric": METRIC,
             "value": value, "unit": "Gtuples/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
@@ -405,9 +442,10 @@ def main():
         if not args.no_extras and world == 1:
             # the other hot-path rows, measured live on the same GPU
             del h_in, h_out
-            out["groupby"] = bench_groupby(gj, wl, peak)
-            out["one_query"] = bench_one_query(gj, wl)
-            out["batched"] = bench_batch(gj, wl)
+            cpu = not args.no_cpu_baseline
+            out["groupby"] = bench_groupby(gj, wl, peak, cpu=cpu)
+            out["one_query"] = bench_one_query(gj, wl, cpu=cpu)
+            out["batched"] = bench_batch(gj, wl, cpu=cpu)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
