@@ -1,22 +1,24 @@
 // radix-partition (paper Sec. 2.3): stable partition of a key column and any
 // number of payload columns on bits [lo, hi) of the key, partitions stored
-// contiguously. One read of the keys builds the digit histogram of every pass
-// (the paper's "histogram pass"); then each pass of <= 8 bits reads key and
-// columns once and writes them once, sequentially.
+// contiguously. Each pass of <= 8 bits reads key and columns once and writes
+// them once.
 //
-// A pass works on tiles taken in order from an atomic counter. Thread 0 of a
-// block issues bulk asynchronous copies (cp.async.bulk, completion on an
-// mbarrier) of the tile's key and every payload column into shared memory, so a
-// whole tile is in flight at once. Keys are ranked stably per warp with
+// Per pass, a histogram kernel counts the digits of every tile of the pass's
+// input (the paper's "histogram pass", per tile), and one block per digit scans
+// those counts: every tile then knows where its rows of each digit go before the
+// scatter starts, so tiles need no ordering or waiting between them. In the
+// scatter, thread 0 of a block bulk-copies (cp.async.bulk, completion on an
+// mbarrier) the tile's key into shared memory and prefetches its payload columns
+// into L2 (cp.async.bulk.prefetch.L2). Keys are ranked stably per warp with
 // match.any (the warp's rows are contiguous, lanes in row order); per-digit warp
-// counts give each row its position inside the tile's digit-sorted order, and a
-// decoupled look-back over tiles (one 32-bit word per tile and digit: 2-bit flag,
-// 30-bit count) gives the global offset of the tile's run of every digit. Every
-// column is then written in sorted order through an inverse index, so warps
-// store contiguous runs of each digit.
+// counts give each row its position inside the tile's digit-sorted order. Every
+// column is then gathered and written in that order through one permutation word
+// per row, so warps store contiguous runs of each digit.
 //
 // Moving every payload column with the key in the same pass is what the GFTR
-// pattern needs (Sec. 4.1.2): one rank computation places all columns.
+// pattern needs (Sec. 4.1.2): one rank computation places all columns. Four
+// 4-byte columns can be written interleaved as one 16-byte row (ColSet::zip4),
+// which later passes and the join's probe move with one access per row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
