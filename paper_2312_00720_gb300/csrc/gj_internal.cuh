@@ -243,6 +243,9 @@ struct Aggs {
   const void* src[kMaxAggs];  // value column of aggregate j (unused for COUNT)
   int32_t size[kMaxAggs];     // 4 or 8
   int64_t* out[kMaxAggs];
+  // GFUR: row r's values are at src[j][tid[r]] (the rows were moved with their
+  // tuple ids only); null: at src[j][r]
+  const int32_t* tid;
 };
 
 __host__ __device__ __forceinline__ int64_t agg_identity(int op) {
@@ -257,7 +260,8 @@ __device__ __forceinline__ int64_t agg_combine(int op, int64_t a, int64_t b) {
 }
 // The value row `row` contributes to aggregate j (COUNT contributes 1).
 __device__ __forceinline__ int64_t agg_value(const Aggs& A, int j, int64_t row) {
-  return A.op[j] == GJ_AGG_COUNT ? 1 : load_as_i64(A.src[j], A.size[j], row);
+  if (A.op[j] == GJ_AGG_COUNT) return 1;
+  return load_as_i64(A.src[j], A.size[j], A.tid ? (int64_t)A.tid[row] : row);
 }
 __device__ __forceinline__ void agg_atomic(int op, int64_t* p, int64_t v) {
   switch (op) {
@@ -274,10 +278,12 @@ struct ColCache {
   int32_t n;
   const int32_t* src[kColCache];
   int8_t slot[kMaxAggs];
+  const int32_t* tid;  // Aggs::tid
 };
 
 inline ColCache make_col_cache(const Aggs& A) {
   ColCache cc{};
+  cc.tid = A.tid;
   for (int j = 0; j < A.n; ++j) {
     cc.slot[j] = -1;
     if (A.op[j] == GJ_AGG_COUNT || A.size[j] != 4) continue;
@@ -298,10 +304,13 @@ inline ColCache make_col_cache(const Aggs& A) {
 template <int B>
 __device__ __forceinline__ void load_cached(const ColCache& cc, const int64_t (&row)[B], const bool (&valid)[B],
                                             int32_t (&cv)[kColCache][B]) {
+  int64_t r[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u) r[u] = (cc.tid && valid[u] && cc.n > 0) ? (int64_t)__ldcs(cc.tid + row[u]) : row[u];
 #pragma unroll
   for (int s = 0; s < kColCache; ++s)
 #pragma unroll
-    for (int u = 0; u < B; ++u) cv[s][u] = (s < cc.n && valid[u]) ? __ldcs(cc.src[s] + row[u]) : 0;
+    for (int u = 0; u < B; ++u) cv[s][u] = (s < cc.n && valid[u]) ? (cc.tid ? __ldg(cc.src[s] + r[u]) : __ldcs(cc.src[s] + r[u])) : 0;
 }
 
 template <int B>
@@ -312,7 +321,7 @@ __device__ __forceinline__ int64_t cached_value(const Aggs& A, const ColCache& c
   if (s == 0) return cv[0][u];
   if (s == 1) return cv[1][u];
   if (s == 2) return cv[2][u];
-  return load_as_i64(A.src[j], A.size[j], row);
+  return load_as_i64(A.src[j], A.size[j], A.tid ? (int64_t)A.tid[row] : row);
 }
 
 // ------------------------------------------------------------------ host side

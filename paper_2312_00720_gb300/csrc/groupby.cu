@@ -258,6 +258,7 @@ struct SegCols {
   int32_t n;
   const int32_t* src[kSegCache];
   int8_t slot[kMaxAggs];
+  const int32_t* tid;  // GFUR: values of sorted row r at src[tid[r]]
 };
 
 // Aggregate OP over value source SLOT (a cached column, or -1: read through
@@ -274,7 +275,7 @@ struct SegOp {
                                             int64_t row) {
     if (OP == GJ_AGG_COUNT) return 1;
     if (SLOT >= 0) return cv[SLOT][r];
-    return (T)load_as_i64(A.src[j], A.size[j], row);
+    return (T)load_as_i64(A.src[j], A.size[j], A.tid ? (int64_t)A.tid[row] : row);
   }
   static __device__ __forceinline__ T comb(T a, T b) {
     if (OP == GJ_AGG_MIN) return a < b ? a : b;
@@ -356,6 +357,19 @@ __device__ __forceinline__ uint32_t seg_heads(const K* __restrict__ key, int64_t
 // Up to kSegCache 4-byte value columns of a lane's rows [r0, nvalid) into registers.
 __device__ __forceinline__ void seg_load_cols(const SegCols& sc, int64_t rb, int r0, int nvalid,
                                               int32_t (&cv)[kSegCache][kSegItems]) {
+  if (sc.tid) {
+    // GFUR: the rows' tuple ids first, then every column gathered through them
+    int32_t id[kSegItems];
+#pragma unroll
+    for (int r = 0; r < kSegItems; ++r) id[r] = (sc.n > 0 && r >= r0 && r < nvalid) ? __ldcs(sc.tid + rb + r) : 0;
+#pragma unroll
+    for (int s = 0; s < kSegCache; ++s) {
+      if (s >= sc.n) break;
+#pragma unroll
+      for (int r = 0; r < kSegItems; ++r) cv[s][r] = (r >= r0 && r < nvalid) ? __ldg(sc.src[s] + id[r]) : 0;
+    }
+    return;
+  }
 #pragma unroll
   for (int s = 0; s < kSegCache; ++s) {
     if (s >= sc.n) break;
@@ -1120,28 +1134,38 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     return cuda_check(cudaGetLastError());
   }
 
-  // ---- SGB-TR and PGB-TR: move the key with every aggregated column (GFTR)
+  // ---- SGB and PGB. TR (GFTR): move the key with every aggregated column; UR
+  // (GFUR): move the key with a generated tuple id and read the values through it
+  const bool ur = variant == GJ_GB_SGB_UR || variant == GJ_GB_PGB_UR;
   ColSet cs{};
   int colmap[kMaxCols];
   for (int c = 0; c < kMaxCols; ++c) colmap[c] = -1;
-  for (int j = 0; j < nagg; ++j) {
-    if (ops[j] == GJ_AGG_COUNT || colmap[op_col[j]] >= 0) continue;
-    int c = op_col[j];
-    colmap[c] = cs.n;
-    cs.src[cs.n] = in->cols[c];
-    cs.size[cs.n] = dtype_size(in->col_type[c]);
-    cs.dst[cs.n] = scr.get((size_t)n * cs.size[cs.n]);
-    cs.n++;
+  if (ur) {
+    cs.n = 1;
+    cs.src[0] = nullptr;  // generated tuple ids
+    cs.size[0] = 4;
+    cs.dst[0] = scr.get((size_t)n * 4);
+  } else {
+    for (int j = 0; j < nagg; ++j) {
+      if (ops[j] == GJ_AGG_COUNT || colmap[op_col[j]] >= 0) continue;
+      int c = op_col[j];
+      colmap[c] = cs.n;
+      cs.src[cs.n] = in->cols[c];
+      cs.size[cs.n] = dtype_size(in->col_type[c]);
+      cs.dst[cs.n] = scr.get((size_t)n * cs.size[cs.n]);
+      cs.n++;
+    }
   }
   K* k2 = scr.get_as<K>(n);
   if (scr.failed()) return GJ_ERR_OOM;
   const void* moved[kMaxCols] = {nullptr};
   for (int c = 0; c < kMaxCols; ++c)
     if (colmap[c] >= 0) moved[c] = cs.dst[colmap[c]];
-  Aggs A = make_aggs(in, nagg, ops, op_col, out_aggs, moved);
+  Aggs A = make_aggs(in, nagg, ops, op_col, out_aggs, ur ? in->cols : moved);
+  if (ur) A.tid = (const int32_t*)cs.dst[0];
   const int kbits = sizeof(K) * 8;
 
-  if (variant == GJ_GB_SGB) {
+  if (variant == GJ_GB_SGB || variant == GJ_GB_SGB_UR) {
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, in->key, k2, cs, n, 0, kbits,
                                   kSignedOrder, opt->bits_per_pass)) != GJ_OK)
       return st;
@@ -1163,6 +1187,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     }
     // the distinct 4-byte value columns (up to kSegCache) are kept in registers
     SegCols sc{};
+    sc.tid = A.tid;
     for (int j = 0; j < nagg; ++j) {
       sc.slot[j] = -1;
       if (ops[j] == GJ_AGG_COUNT || A.size[j] != 4) continue;
@@ -1193,7 +1218,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     return cuda_check(cudaGetLastError());
   }
 
-  // PGB-TR: partitions of about 2048 rows on hashed key bits (at most 16 bits)
+  // PGB-TR / PGB-UR: partitions of about 2048 rows on hashed key bits (at most 16 bits)
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : 0;
   if (opt->radix_bits <= 0)
     while (bits < 16 && (n >> bits) > 2048) ++bits;
@@ -1205,10 +1230,14 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   } else {
     if ((st = cuda_check(cudaMemcpyAsync(k2, in->key, sizeof(K) * n, cudaMemcpyDeviceToDevice, s))) != GJ_OK)
       return st;
-    for (int c = 0; c < cs.n; ++c)
-      if ((st = cuda_check(cudaMemcpyAsync(cs.dst[c], cs.src[c], (size_t)n * cs.size[c], cudaMemcpyDeviceToDevice,
-                                           s))) != GJ_OK)
-        return st;
+    if (ur) {
+      A.tid = nullptr;  // one partition: rows keep their order
+    } else {
+      for (int c = 0; c < cs.n; ++c)
+        if ((st = cuda_check(cudaMemcpyAsync(cs.dst[c], cs.src[c], (size_t)n * cs.size[c],
+                                             cudaMemcpyDeviceToDevice, s))) != GJ_OK)
+          return st;
+    }
   }
   int64_t* poff = scr.get_as<int64_t>(nparts + 1);
   int64_t* gcount = scr.get_as<int64_t>(nparts + 1);

@@ -1,5 +1,6 @@
-"""Group-by variants (HGB Alg. 1, SGB-TR, PGB-TR) through the C-ABI vs the oracle:
-canonically sorted (key, aggregates) rows must be identical."""
+"""Group-by variants (HGB Alg. 1, SGB-TR, PGB-TR and their GFUR halves SGB-UR,
+PGB-UR) through the C-ABI vs the oracle: canonically sorted (key, aggregates) rows
+must be identical."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +10,7 @@ from paper_2312_00720_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["hgb", "sgb", "pgb"]
+VARIANTS = ["hgb", "sgb", "pgb", "sgb_ur", "pgb_ur"]
 AGGS = ["count", "sum", "min", "max", "sum", "min", "max", "sum", "min", "max"]
 COLS = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
 
@@ -52,19 +53,29 @@ def test_int64_values_and_negative_keys(gj, variant):
     assert np.array_equal(got, want_rows(key, vals, aggs, cols))
 
 
-def test_sgb_output_is_sorted_and_deterministic(gj):
+@pytest.mark.parametrize("variant", ["sgb", "sgb_ur"])
+def test_sgb_output_is_sorted_and_deterministic(gj, variant):
     w = wl.groupby_workload(200000, 5000, nvals=2, seed=2)
-    a = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], "sgb")
-    b = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], "sgb")
+    a = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], variant)
+    b = run_gb(gj, w["key"], w["vals"], ["sum", "max"], [0, 1], variant)
     assert np.array_equal(a, b)
     assert np.all(np.diff(a[:, 0]) > 0)
 
 
-def test_pgb_sub_rounds_when_partition_overflows(gj):
+@pytest.mark.parametrize("variant", ["pgb", "pgb_ur"])
+def test_pgb_sub_rounds_when_partition_overflows(gj, variant):
     # one hashed bit gives partitions of ~100K distinct keys, far above one table
     w = wl.groupby_workload(400000, 200000, nvals=1, seed=9)
-    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], ["count", "sum"], [0, 0], "pgb", radix_bits=1))
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], ["count", "sum"], [0, 0], variant, radix_bits=1))
     assert np.array_equal(got, want_rows(w["key"], w["vals"], ["count", "sum"], [0, 0]))
+
+
+def test_sgb_ur_and_tr_give_identical_rows(gj):
+    # both sort the keys the same way; only how the values travel differs
+    w = wl.groupby_workload(300000, 3000, nvals=3, seed=21)
+    a = run_gb(gj, w["key"], w["vals"], AGGS, COLS, "sgb")
+    b = run_gb(gj, w["key"], w["vals"], AGGS, COLS, "sgb_ur")
+    assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
