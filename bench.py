@@ -160,7 +160,7 @@ def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20, cpu: bool
     min_bytes = n * (4 + 12) + distinct * (4 + 80)
     out = {"workload": f"n=2^27 int32 keys over 2^{log2_groups} ids ({distinct} groups), 3 int32 values, "
                        f"COUNT+SUM/MIN/MAX per column", "min_bytes": min_bytes}
-    for v in ("hgb", "sgb", "pgb", "sgb_ur", "pgb_ur"):
+    for v in ("hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"):
         okeys, outs, ng = gj.groupby(key, vals, aggs, cols, variant=v, sync=True)
         assert int(ng.item()) == distinct
         ms = _event_ms(lambda: gj.groupby(key, vals, aggs, cols, variant=v, sync=False), steps)

@@ -86,7 +86,10 @@ typedef enum {
   GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3) */
   GJ_GB_PGB = 3, /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3) */
   GJ_GB_SGB_UR = 4, /* SGB with (key, tuple id) sorted and values gathered through the ids (GFUR, Sec. 4.1.2) */
-  GJ_GB_PGB_UR = 5  /* PGB with (key, tuple id) partitioned and values gathered through the ids (GFUR) */
+  GJ_GB_PGB_UR = 5, /* PGB with (key, tuple id) partitioned and values gathered through the ids (GFUR) */
+  GJ_GB_SGB_DE = 6  /* SGB on dictionary codes: dense group ids (HGB stage 1) sorted on ceil(log2 g) bits
+                       with the values, keys decoded from the dictionary (Sec. 4.1.3); synchronises the
+                       stream once to read g */
 } gj_groupby_variant;
 
 typedef enum { GJ_SELECT_HEURISTIC = 0, GJ_SELECT_MLP = 1 } gj_selector_mode;

@@ -287,7 +287,7 @@ gj_status gj_groupby(const gj_table* in, int32_t nagg, const int32_t* ops, const
   gj_options defaults;
   gj_options_default(&defaults);
   if (!opt) opt = &defaults;
-  if (opt->groupby_variant < GJ_GB_AUTO || opt->groupby_variant > GJ_GB_PGB_UR) return GJ_ERR_INVALID_ARG;
+  if (opt->groupby_variant < GJ_GB_AUTO || opt->groupby_variant > GJ_GB_SGB_DE) return GJ_ERR_INVALID_ARG;
   if (opt->radix_bits < 0 || opt->radix_bits > 24 || opt->bits_per_pass < 0 || opt->bits_per_pass > 8)
     return GJ_ERR_INVALID_ARG;
   Ctx ctx;

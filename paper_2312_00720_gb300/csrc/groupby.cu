@@ -1077,6 +1077,73 @@ Aggs make_aggs(const gj_table* in, int nagg, const int32_t* ops, const int32_t* 
   return A;
 }
 
+// The segmented reduction over sorted keys k2 (SGB): tile records, their
+// two-level scan, then one walk of the rows; group keys go to out_keys in
+// sorted order, aggregates to A.out, the group count to d_ngroups.
+template <typename K>
+gj_status sgb_reduce_run(const Ctx& ctx, Scratch& scr, const K* k2, int64_t n, const Aggs& A, int nagg,
+                         const int32_t* ops, K* out_keys, int64_t cap, int64_t* d_ngroups) {
+  cudaStream_t s = ctx.stream;
+  const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
+  const int64_t nblk = (ntiles + kScanBlock - 1) / kScanBlock;  // <= kScanBlock while n < 2^32
+  const int rw = nagg + 2;
+  int64_t* rec = scr.get_as<int64_t>((size_t)ntiles * rw);
+  int64_t* carry = scr.get_as<int64_t>((size_t)ntiles * rw);
+  int64_t* btot = scr.get_as<int64_t>((size_t)nblk * rw);
+  int64_t* bcarry = scr.get_as<int64_t>((size_t)nblk * rw);
+  if (scr.failed()) return GJ_ERR_OOM;
+  const size_t dyn = sizeof(int64_t) * ((size_t)2 * kSegWarps * nagg * 32 + (size_t)2 * kSegWarps * rw);
+  static bool attr[2] = {false, false};
+  if (!attr[sizeof(K) == 8]) {
+    cudaFuncSetAttribute(
+        sgb_reduce_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(sizeof(int64_t) * ((size_t)2 * kSegWarps * kMaxAggs * 32 + 2 * kSegWarps * (kMaxAggs + 2))));
+    attr[sizeof(K) == 8] = true;
+  }
+  // the distinct 4-byte value columns (up to kSegCache) are kept in registers
+  SegCols sc{};
+  sc.tid = A.tid;
+  for (int j = 0; j < nagg; ++j) {
+    sc.slot[j] = -1;
+    if (ops[j] == GJ_AGG_COUNT || A.size[j] != 4) continue;
+    int s2 = -1;
+    for (int q = 0; q < sc.n; ++q)
+      if (sc.src[q] == A.src[j]) s2 = q;
+    if (s2 < 0 && sc.n < kSegCache) {
+      s2 = sc.n;
+      sc.src[sc.n++] = (const int32_t*)A.src[j];
+    }
+    sc.slot[j] = (int8_t)s2;
+  }
+  {
+    LaunchScope ls(ctx, KK_SGB_REDUCE);
+    sgb_tile_kernel<K><<<(unsigned)ntiles, kSegWarps * 32, 0, s>>>(k2, n, A, sc, rec);
+  }
+  {
+    LaunchScope ls(ctx, KK_SGB_REDUCE);
+    sgb_scan_kernel<<<(unsigned)nblk, kScanBlock, 0, s>>>(rec, ntiles, A, carry, btot, nullptr);
+  }
+  {
+    LaunchScope ls(ctx, KK_SGB_REDUCE);
+    sgb_scan_kernel<<<1, kScanBlock, 0, s>>>(btot, nblk, A, bcarry, nullptr, d_ngroups);
+  }
+  LaunchScope ls(ctx, KK_SGB_REDUCE);
+  sgb_reduce_kernel<K><<<(unsigned)ntiles, kSegWarps * 32, dyn, s>>>(k2, n, A, sc, out_keys, cap, carry, bcarry,
+                                                                     ctx.d_status);
+  return cuda_check(cudaGetLastError());
+}
+
+// code[i] = the dense group id of row i (HGB stage 1: gid_of_row at the row its key
+// was inserted with), the dictionary code SGB-DE sorts.
+__global__ void de_codes_kernel(const int32_t* __restrict__ gidloc, const int32_t* __restrict__ gid_of_row, int64_t n,
+                                int32_t* __restrict__ code) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int32_t loc = gidloc[i];
+    code[i] = loc >= 0 ? gid_of_row[loc] : 0;  // a failed insert has set the status already
+  }
+}
+
 template <typename K>
 gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int32_t* ops, const int32_t* op_col,
                         const gj_options* opt, int variant, void* out_keys, int64_t* const* out_aggs, int64_t cap,
@@ -1134,6 +1201,61 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     return cuda_check(cudaGetLastError());
   }
 
+  // ---- SGB-DE (Sec. 4.1.3 with dictionary encoding): HGB stage 1 gives every
+  // row a dense code and writes the dictionary (code -> key) to out_keys; the
+  // codes are then sorted with the values on their ceil(log2 g) bits only and
+  // reduced by the SGB kernels, whose segment i is code i. Reading g to size the
+  // sort synchronises the stream once.
+  if (variant == GJ_GB_SGB_DE) {
+    uint64_t want = (uint64_t)std::max<int64_t>(2, 2 * (opt->groups_hint > 0 ? std::min(opt->groups_hint, n) : n));
+    uint64_t slots = 1;
+    while (slots < want) slots <<= 1;
+    int32_t* ht = scr.get_as<int32_t>(slots);
+    int32_t* gid_of_row = scr.get_as<int32_t>(n);
+    int32_t* gidloc = scr.get_as<int32_t>(n);
+    int32_t* code = scr.get_as<int32_t>(n);
+    int32_t* code2 = scr.get_as<int32_t>(n);
+    int32_t* code_out = scr.get_as<int32_t>(n);  // the reduction's segment codes (0, 1, ...), unused
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
+    {
+      LaunchScope ls(ctx, KK_HGB_GROUP_ID);
+      int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx.num_sms * 8);
+      hgb_group_id_kernel<K><<<blocks, 256, 0, s>>>((const K*)in->key, n, ht, slots - 1, gid_of_row, gidloc,
+                                                     (unsigned long long*)d_ngroups, (K*)out_keys, cap,
+                                                     ctx.d_status);
+      de_codes_kernel<<<blocks, 256, 0, s>>>(gidloc, gid_of_row, n, code);
+    }
+    int64_t g = 0;
+    if ((st = cuda_check(cudaMemcpyAsync(&g, d_ngroups, sizeof(int64_t), cudaMemcpyDeviceToHost, s))) != GJ_OK)
+      return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s))) != GJ_OK) return st;
+    g = std::min<int64_t>(std::max<int64_t>(g, 1), std::min<int64_t>(n, cap));
+    int bits = 1;
+    while ((int64_t(1) << bits) < g) ++bits;
+    ColSet cs{};
+    int colmap[kMaxCols];
+    for (int c = 0; c < kMaxCols; ++c) colmap[c] = -1;
+    for (int j = 0; j < nagg; ++j) {
+      if (ops[j] == GJ_AGG_COUNT || colmap[op_col[j]] >= 0) continue;
+      int c = op_col[j];
+      colmap[c] = cs.n;
+      cs.src[cs.n] = in->cols[c];
+      cs.size[cs.n] = dtype_size(in->col_type[c]);
+      cs.dst[cs.n] = scr.get((size_t)n * cs.size[cs.n]);
+      cs.n++;
+    }
+    if (scr.failed()) return GJ_ERR_OOM;
+    const void* moved[kMaxCols] = {nullptr};
+    for (int c = 0; c < kMaxCols; ++c)
+      if (colmap[c] >= 0) moved[c] = cs.dst[colmap[c]];
+    Aggs A = make_aggs(in, nagg, ops, op_col, out_aggs, moved);
+    if ((st = radix_partition_run(ctx, scr, GJ_I32, code, code2, cs, n, 0, bits, kRawBits, opt->bits_per_pass)) !=
+        GJ_OK)
+      return st;
+    return sgb_reduce_run<int32_t>(ctx, scr, code2, n, A, nagg, ops, code_out, cap, d_ngroups);
+  }
+
   // ---- SGB and PGB. TR (GFTR): move the key with every aggregated column; UR
   // (GFUR): move the key with a generated tuple id and read the values through it
   const bool ur = variant == GJ_GB_SGB_UR || variant == GJ_GB_PGB_UR;
@@ -1169,53 +1291,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, in->key, k2, cs, n, 0, kbits,
                                   kSignedOrder, opt->bits_per_pass)) != GJ_OK)
       return st;
-    const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
-    const int64_t nblk = (ntiles + kScanBlock - 1) / kScanBlock;  // <= kScanBlock while n < 2^32
-    const int rw = nagg + 2;
-    int64_t* rec = scr.get_as<int64_t>((size_t)ntiles * rw);
-    int64_t* carry = scr.get_as<int64_t>((size_t)ntiles * rw);
-    int64_t* btot = scr.get_as<int64_t>((size_t)nblk * rw);
-    int64_t* bcarry = scr.get_as<int64_t>((size_t)nblk * rw);
-    if (scr.failed()) return GJ_ERR_OOM;
-    const size_t dyn = sizeof(int64_t) * ((size_t)2 * kSegWarps * nagg * 32 + (size_t)2 * kSegWarps * rw);
-    static bool attr[2] = {false, false};
-    if (!attr[sizeof(K) == 8]) {
-      cudaFuncSetAttribute(
-          sgb_reduce_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-          (int)(sizeof(int64_t) * ((size_t)2 * kSegWarps * kMaxAggs * 32 + 2 * kSegWarps * (kMaxAggs + 2))));
-      attr[sizeof(K) == 8] = true;
-    }
-    // the distinct 4-byte value columns (up to kSegCache) are kept in registers
-    SegCols sc{};
-    sc.tid = A.tid;
-    for (int j = 0; j < nagg; ++j) {
-      sc.slot[j] = -1;
-      if (ops[j] == GJ_AGG_COUNT || A.size[j] != 4) continue;
-      int s2 = -1;
-      for (int q = 0; q < sc.n; ++q)
-        if (sc.src[q] == A.src[j]) s2 = q;
-      if (s2 < 0 && sc.n < kSegCache) {
-        s2 = sc.n;
-        sc.src[sc.n++] = (const int32_t*)A.src[j];
-      }
-      sc.slot[j] = (int8_t)s2;
-    }
-    {
-      LaunchScope ls(ctx, KK_SGB_REDUCE);
-      sgb_tile_kernel<K><<<(unsigned)ntiles, kSegWarps * 32, 0, s>>>(k2, n, A, sc, rec);
-    }
-    {
-      LaunchScope ls(ctx, KK_SGB_REDUCE);
-      sgb_scan_kernel<<<(unsigned)nblk, kScanBlock, 0, s>>>(rec, ntiles, A, carry, btot, nullptr);
-    }
-    {
-      LaunchScope ls(ctx, KK_SGB_REDUCE);
-      sgb_scan_kernel<<<1, kScanBlock, 0, s>>>(btot, nblk, A, bcarry, nullptr, d_ngroups);
-    }
-    LaunchScope ls(ctx, KK_SGB_REDUCE);
-    sgb_reduce_kernel<K><<<(unsigned)ntiles, kSegWarps * 32, dyn, s>>>(k2, n, A, sc, (K*)out_keys, cap, carry,
-                                                                       bcarry, ctx.d_status);
-    return cuda_check(cudaGetLastError());
+    return sgb_reduce_run<K>(ctx, scr, k2, n, A, nagg, ops, (K*)out_keys, cap, d_ngroups);
   }
 
   // PGB-TR / PGB-UR: partitions of about 2048 rows on hashed key bits (at most 16 bits)

@@ -1,6 +1,6 @@
-"""Group-by variants (HGB Alg. 1, SGB-TR, PGB-TR and their GFUR halves SGB-UR,
-PGB-UR) through the C-ABI vs the oracle: canonically sorted (key, aggregates) rows
-must be identical."""
+"""Group-by variants (HGB Alg. 1, SGB-TR, PGB-TR, their GFUR halves SGB-UR, PGB-UR,
+and SGB-DE on dictionary codes) through the C-ABI vs the oracle: canonically
+sorted (key, aggregates) rows must be identical."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +10,7 @@ from paper_2312_00720_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["hgb", "sgb", "pgb", "sgb_ur", "pgb_ur"]
+VARIANTS = ["hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"]
 AGGS = ["count", "sum", "min", "max", "sum", "min", "max", "sum", "min", "max"]
 COLS = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
 
@@ -68,6 +68,15 @@ def test_pgb_sub_rounds_when_partition_overflows(gj, variant):
     w = wl.groupby_workload(400000, 200000, nvals=1, seed=9)
     got = oracle.canonical(run_gb(gj, w["key"], w["vals"], ["count", "sum"], [0, 0], variant, radix_bits=1))
     assert np.array_equal(got, want_rows(w["key"], w["vals"], ["count", "sum"], [0, 0]))
+
+
+def test_sgb_de_groups_follow_the_dictionary(gj):
+    # SGB-DE writes group i at the dictionary code i: its keys are distinct and
+    # the aggregates sit beside their own key
+    w = wl.groupby_workload(250000, 1 << 14, nvals=1, seed=31)
+    rows = run_gb(gj, w["key"], w["vals"], ["count", "sum"], [0, 0], "sgb_de")
+    assert np.unique(rows[:, 0]).size == rows.shape[0]
+    assert np.array_equal(oracle.canonical(rows), want_rows(w["key"], w["vals"], ["count", "sum"], [0, 0]))
 
 
 def test_sgb_ur_and_tr_give_identical_rows(gj):
