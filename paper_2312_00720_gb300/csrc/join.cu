@@ -677,6 +677,134 @@ __global__ void __launch_bounds__(kThreads) nphj_probe_kernel(const K* __restric
   emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
 }
 
+// ---------------------------------------------------------------- NPHJ, many-to-many
+// R.key may repeat (Sec. 5.1, many-to-many joins). The global table keeps, per
+// key, the last R row inserted (row + 1); next[r] links each R row to the one
+// inserted before it with the same key (-1 ends the chain), so the rows of a key
+// are one chain. Chain order follows the insertions and is not fixed, which only
+// reorders T.
+template <typename K>
+__global__ void nphj_mn_build_kernel(const K* __restrict__ rkey, int64_t nr, int32_t* __restrict__ ht, uint64_t mask,
+                                     int32_t* __restrict__ next, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+    const K k = rkey[i];
+    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    bool done = false;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      const int prev = atomicCAS(&ht[sl], 0, (int)(i + 1));
+      if (prev == 0) {
+        next[i] = -1;
+        done = true;
+        break;
+      }
+      if (rkey[prev - 1] == k) {
+        // the key's slot: this row becomes the head, linked to the previous head
+        next[i] = atomicExch(&ht[sl], (int)(i + 1)) - 1;
+        done = true;
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+    if (!done) set_status(err, GJ_ERR_CAPACITY);
+  }
+}
+
+// One block per tile of kTileS probe rows (a contiguous run of kItems rows per
+// thread): count every row's matches by walking its key's chain, take the tile's
+// output offset from a decoupled look-back over tiles, then walk the chains again
+// and write each (r, s) pair. Output rows of a thread are contiguous.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) nphj_mn_probe_kernel(const K* __restrict__ rkey,
+                                                                 const int32_t* __restrict__ ht, uint64_t mask,
+                                                                 const int32_t* __restrict__ next,
+                                                                 const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                                 uint64_t* tile_status, int* tile_counter,
+                                                                 int64_t ntiles, int* err) {
+  __shared__ uint64_t s_warp[kThreads / 32];
+  __shared__ uint64_t s_base;
+  __shared__ int64_t s_tile;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = atomicAdd(tile_counter, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t r0 = tile * kTileS + (int64_t)t * kItems;  // this thread's rows [r0, r0 + kItems)
+  int32_t head[kItems];
+  uint32_t cnt[kItems];
+  uint64_t mine = 0;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = r0 + j;
+    head[j] = -1;
+    cnt[j] = 0;
+    if (i >= ns) continue;
+    const K k = skey[i];
+    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+      const int v = __ldg(ht + sl);
+      if (v == 0) break;
+      if (__ldg(rkey + v - 1) == k) {
+        head[j] = v - 1;
+        break;
+      }
+      sl = (sl + 1) & mask;
+    }
+    for (int32_t r = head[j]; r >= 0; r = __ldg(next + r)) ++cnt[j];
+    mine += cnt[j];
+  }
+  // block exclusive scan of the per-thread match counts, then the tile's offset
+  uint64_t x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < kThreads / 32 ? s_warp[lane] : 0;
+    uint64_t wx = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, wx, o);
+      if (lane >= o) wx += y;
+    }
+    const uint64_t total = __shfl_sync(0xffffffffu, wx, 31);
+    if (lane < kThreads / 32) s_warp[lane] = wx - w;
+    const uint64_t excl = lookback_scan_warp(tile_status, tile, total, err);
+    if (lane == 0) {
+      s_base = excl;
+      if (tile == ntiles - 1 && io.d_count) *io.d_count = (int64_t)(excl + total);
+    }
+  }
+  __syncthreads();
+  uint64_t pos = s_base + s_warp[warp] + (x - mine);
+  const int ncols = io.nr_cols + io.ns_cols;
+  bool overflow = false;
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int64_t i = r0 + j;
+    if (i >= ns) continue;
+    const K k = head[j] >= 0 ? skey[i] : K(0);
+    for (int32_t r = head[j]; r >= 0; r = __ldg(next + r)) {
+      if ((int64_t)pos >= io.cap) {
+        overflow = true;
+        break;
+      }
+      ((K*)io.tkey)[pos] = k;
+      for (int c = 0; c < ncols; ++c) {
+        const bool rside = c < io.nr_cols;
+        const int sz = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
+        const int64_t src_row = rside ? (int64_t)r : i;
+        const void* src = rside ? io.rsrc[c] : io.ssrc[c - io.nr_cols];
+        copy_elem(io.tcols[c], (int64_t)pos, src, src_row, sz);
+      }
+      ++pos;
+    }
+  }
+  if (overflow) set_status(err, GJ_ERR_CAPACITY);
+}
+
 // ---------------------------------------------------------------- join -> group-by
 // The group-by that follows a join (Sec. 1) fused into the probe: each match is
 // aggregated where it is found and T is never written. Groups live either in a
@@ -932,6 +1060,27 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if (scr.failed()) return GJ_ERR_OOM;
   if ((st = cuda_check(cudaMemsetAsync(tstat, 0, sizeof(uint64_t) * ntiles, s))) != GJ_OK) return st;
   if ((st = cuda_check(cudaMemsetAsync(counter, 0, sizeof(int), s))) != GJ_OK) return st;
+
+  if (variant == GJ_JOIN_NPHJ_MN) {
+    uint64_t slots = 1;
+    while (slots < (uint64_t)std::max<int64_t>(2 * nr, 2)) slots <<= 1;
+    int32_t* ht = scr.get_as<int32_t>(slots);
+    int32_t* next = scr.get_as<int32_t>(std::max<int64_t>(nr, 1));
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
+    for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+    for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+    {
+      int blocks = (int)std::min<int64_t>((nr + 255) / 256, (int64_t)ctx.num_sms * 16);
+      LaunchScope ls(ctx, KK_NPHJ_BUILD);
+      nphj_mn_build_kernel<K><<<blocks, 256, 0, s>>>((const K*)R->key, nr, ht, slots - 1, next, ctx.d_status);
+    }
+    LaunchScope ls(ctx, KK_NPHJ_PROBE);
+    nphj_mn_probe_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>((const K*)R->key, ht, slots - 1, next,
+                                                                   (const K*)S->key, ns, io, tstat, counter, ntiles,
+                                                                   ctx.d_status);
+    return cuda_check(cudaGetLastError());
+  }
 
   if (variant == GJ_JOIN_NPHJ) {
     uint64_t slots = 1;

@@ -92,6 +92,20 @@ def join_workload(nr: int, ns: int, ncols_r: int, ncols_s: int, *, theta: float 
     return {"rkey": rkey, "rcols": rcols, "skey": skey, "scols": scols, "n_match": ns - n_miss}
 
 
+def mn_join_workload(nr: int, ns: int, nk: int, ncols_r: int = 2, ncols_s: int = 2, *, key_dtype=np.int32,
+                     col_dtype=np.int32, seed: int = 13):
+    """Many-to-many join inputs: R.key and S.key drawn uniformly from a seeded set
+    of nk distinct keys (Sec. 5.1, many-to-many joins); payloads uniform in [0, 2^31)."""
+    keys = _rng(seed, 0).permutation(max(nk, 1) * 4)[:max(nk, 1)].astype(key_dtype)
+    rkey = keys[_rng(seed, 1).integers(0, max(nk, 1), size=nr)]
+    skey = keys[_rng(seed, 2).integers(0, max(nk, 1), size=ns)]
+    rcols = [_rng(seed, 10 + c).integers(0, 2**31, size=nr, dtype=np.int64).astype(col_dtype)
+             for c in range(ncols_r)]
+    scols = [_rng(seed, 20 + c).integers(0, 2**31, size=ns, dtype=np.int64).astype(col_dtype)
+             for c in range(ncols_s)]
+    return {"rkey": rkey, "rcols": rcols, "skey": skey, "scols": scols}
+
+
 def groupby_workload(n: int, g: int, *, nvals: int = 3, key_dtype=np.int32, theta: float = 0.0,
                      seed: int = 3, lo: int = -(2**20), hi: int = 2**20):
     """Group-by input R(k, r1..r_nvals): keys from a domain of g ids, values uniform in [lo, hi).
