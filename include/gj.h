@@ -78,9 +78,12 @@ typedef enum {
   GJ_JOIN_PHJ_TR = 1, /* radix-partitioned hash join, payloads partitioned with the keys (GFTR, Sec. 4.1.4) */
   GJ_JOIN_PHJ_UR = 2, /* same partitioning of (key, tuple id), payloads gathered by id (GFUR, Sec. 3.1.2, 4.1.4) */
   GJ_JOIN_NPHJ = 3,   /* non-partitioned hash join: global table on R, S probed in order (Sec. 3.1.3) */
-  GJ_JOIN_NPHJ_MN = 4 /* many-to-many (R.key need not be unique, Sec. 5.1): global table on R with a chain
+  GJ_JOIN_NPHJ_MN = 4, /* many-to-many (R.key need not be unique, Sec. 5.1): global table on R with a chain
                          of equal keys; every (r, s) pair is written, |T| = sum over S of its matches.
                          gj_join only; never chosen by AUTO */
+  GJ_JOIN_SMJ_TR = 5, /* sort-merge join: both sides radix-sorted on the whole key with their payloads,
+                         tiles of S merged against their range of R (merge path), Sec. 3.1.1 */
+  GJ_JOIN_SMJ_UR = 6  /* the same with (key, tuple id) sorted and payloads gathered by id (GFUR) */
 } gj_join_variant;
 
 typedef enum {

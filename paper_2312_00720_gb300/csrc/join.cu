@@ -677,6 +677,96 @@ __global__ void __launch_bounds__(kThreads) nphj_probe_kernel(const K* __restric
   emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
 }
 
+// ---------------------------------------------------------------- SMJ
+// Sort-merge join (Sec. 3.1.1; the paper's comparison point, with Merge Path
+// partitioning): R and S are radix-sorted on the whole key (signed order), with
+// their payloads (TR) or tuple ids (UR). Each tile of kTileS sorted S rows finds
+// its range of R rows by two warp-wide 33-way searches over R (the tile's first
+// and last key: the merge-path split points), stages those R keys in shared
+// memory when they fit, and matches every row by binary search in them. The
+// NPHJ emitter then compacts and writes the tile through a decoupled look-back.
+constexpr int kSmjRBytes = 12288;  // staged R keys per tile
+
+// First index in sorted a[0, n) whose element is not below key (Upper: above key),
+// found by all 32 lanes of a warp: 32 pivots per round trip.
+template <typename K, bool Upper>
+__device__ int64_t warp_bound(const K* __restrict__ a, int64_t n, K key) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int64_t len = hi - lo;
+    const int64_t p = lo + (len * (lane + 1)) / 33;
+    const K v = a[p];
+    const bool before = Upper ? !(key < v) : (v < key);  // the answer lies after p
+    const int c = __popc(__ballot_sync(0xffffffffu, before));
+    const int64_t nlo = c == 0 ? lo : lo + (len * c) / 33 + 1;
+    const int64_t nhi = c == 32 ? hi : lo + (len * (c + 1)) / 33;
+    lo = nlo;
+    hi = nhi;
+  }
+  const int64_t p = lo + lane;
+  bool before = false;
+  if (p < hi) {
+    const K v = a[p];
+    before = Upper ? !(key < v) : (v < key);
+  }
+  return lo + __popc(__ballot_sync(0xffffffffu, before));
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) smj_merge_kernel(const K* __restrict__ rkey, int64_t nr,
+                                                             const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                             uint64_t* tile_status, int* tile_counter, int64_t ntiles,
+                                                             int* err) {
+  constexpr int kStageR = kSmjRBytes / (int)sizeof(K);
+  __shared__ K s_key[kTileS];
+  __shared__ K s_r[kStageR];
+  __shared__ int32_t s_pos[kTileS];
+  __shared__ int32_t s_midx[kTileS];
+  __shared__ uint32_t s_scan[kThreads / 32];
+  __shared__ uint64_t s_base;
+  __shared__ int64_t s_tile, s_ra, s_rb;
+  const int t = threadIdx.x;
+  if (t == 0) s_tile = atomicAdd(tile_counter, 1);
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t tile_base = tile * kTileS;
+  const int tile_n = (int)min64(kTileS, ns - tile_base);
+  for (int i = t; i < tile_n; i += kThreads) s_key[i] = __ldcs(skey + tile_base + i);
+  if (t < 32) {
+    // the merge-path split: R rows with keys in [first, last] of the tile
+    const int64_t ra = warp_bound<K, false>(rkey, nr, skey[tile_base]);
+    const int64_t rb = warp_bound<K, true>(rkey, nr, skey[tile_base + tile_n - 1]);
+    if (t == 0) {
+      s_ra = ra;
+      s_rb = rb;
+    }
+  }
+  __syncthreads();
+  const int64_t ra = s_ra, rb = s_rb;
+  const bool staged = rb - ra <= kStageR;
+  if (staged)
+    for (int64_t j = t; j < rb - ra; j += kThreads) s_r[j] = __ldg(rkey + ra + j);
+  __syncthreads();
+  for (int i = t; i < tile_n; i += kThreads) {
+    const K k = s_key[i];
+    int64_t lo = ra, hi = rb;  // first R row in [ra, rb) not below k
+    while (lo < hi) {
+      const int64_t m = (lo + hi) >> 1;
+      const K v = staged ? s_r[m - ra] : rkey[m];
+      if (v < k) lo = m + 1; else hi = m;
+    }
+    int32_t mi = -1;
+    if (lo < rb && (staged ? s_r[lo - ra] : rkey[lo]) == k) {
+      mi = (int32_t)lo;
+      if (lo + 1 < rb && (staged ? s_r[lo + 1 - ra] : rkey[lo + 1]) == k) set_status(err, GJ_ERR_DUPLICATE_KEY);
+    }
+    s_midx[i] = mi;
+  }
+  __syncthreads();
+  emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
+}
+
 // ---------------------------------------------------------------- NPHJ, many-to-many
 // R.key may repeat (Sec. 5.1, many-to-many joins). The global table keeps, per
 // key, the last R row inserted (row + 1); next[r] links each R row to the one
@@ -1060,6 +1150,52 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if (scr.failed()) return GJ_ERR_OOM;
   if ((st = cuda_check(cudaMemsetAsync(tstat, 0, sizeof(uint64_t) * ntiles, s))) != GJ_OK) return st;
   if ((st = cuda_check(cudaMemsetAsync(counter, 0, sizeof(int), s))) != GJ_OK) return st;
+
+  if (variant == GJ_JOIN_SMJ_TR || variant == GJ_JOIN_SMJ_UR) {
+    // sort both sides on every key bit; TR moves the payloads along, UR a tuple id
+    const bool tr = variant == GJ_JOIN_SMJ_TR;
+    const int kbits = sizeof(K) * 8;
+    K* rk2 = scr.get_as<K>(nr);
+    K* sk2 = scr.get_as<K>(ns);
+    ColSet rc{}, sc{};
+    if (tr) {
+      rc.n = R->ncols;
+      for (int c = 0; c < R->ncols; ++c) {
+        rc.src[c] = R->cols[c];
+        rc.size[c] = dtype_size(R->col_type[c]);
+        rc.dst[c] = scr.get((size_t)nr * rc.size[c]);
+      }
+      sc.n = S->ncols;
+      for (int c = 0; c < S->ncols; ++c) {
+        sc.src[c] = S->cols[c];
+        sc.size[c] = dtype_size(S->col_type[c]);
+        sc.dst[c] = scr.get((size_t)ns * sc.size[c]);
+      }
+    } else {
+      rc.n = sc.n = 1;
+      rc.src[0] = sc.src[0] = nullptr;  // generated tuple ids
+      rc.size[0] = sc.size[0] = 4;
+      rc.dst[0] = scr.get((size_t)nr * 4);
+      sc.dst[0] = scr.get((size_t)ns * 4);
+    }
+    if (scr.failed()) return GJ_ERR_OOM;
+    const int kt = sizeof(K) == 8 ? GJ_I64 : GJ_I32;
+    if ((st = radix_partition_run(ctx, scr, kt, R->key, rk2, rc, nr, 0, kbits, kSignedOrder, bpp)) != GJ_OK) return st;
+    if ((st = radix_partition_run(ctx, scr, kt, S->key, sk2, sc, ns, 0, kbits, kSignedOrder, bpp)) != GJ_OK) return st;
+    if (tr) {
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = rc.dst[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = sc.dst[c];
+    } else {
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+      io.r_tid = (const int32_t*)rc.dst[0];
+      io.s_tid = (const int32_t*)sc.dst[0];
+    }
+    LaunchScope ls(ctx, KK_PHJ_PROBE);
+    smj_merge_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>(rk2, nr, sk2, ns, io, tstat, counter, ntiles,
+                                                               ctx.d_status);
+    return cuda_check(cudaGetLastError());
+  }
 
   if (variant == GJ_JOIN_NPHJ_MN) {
     uint64_t slots = 1;

@@ -9,7 +9,7 @@ from paper_2312_00720_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["phj_tr", "phj_ur", "nphj"]
+VARIANTS = ["phj_tr", "phj_ur", "nphj", "smj_tr", "smj_ur"]
 
 
 def run_join(gj, w, variant, **kw):
@@ -60,6 +60,14 @@ def test_radix_bits_do_not_change_result(gj, bits, bpp):
     for v in ("phj_tr", "phj_ur"):
         got = oracle.canonical(run_join(gj, w, v, radix_bits=bits, bits_per_pass=bpp))
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", ["smj_tr", "smj_ur"])
+def test_sort_merge_with_a_large_build_range_per_tile(gj, variant):
+    # |R| >> |S|: a tile's keys span far more R rows than the shared-memory stage
+    # holds, so the merge searches R in global memory
+    w = wl.join_workload(1 << 20, 5000, 2, 2, mr=0.9, seed=12)
+    assert np.array_equal(oracle.canonical(run_join(gj, w, variant)), oracle.canonical(oracle_rows(w)))
 
 
 def test_build_partition_larger_than_shared_memory_table(gj):
