@@ -64,7 +64,7 @@ cudaEvent_t take_event() {
 const char* const kKindNames[KK_COUNT] = {
     "radix_hist", "radix_scatter", "partition_bounds", "phj_probe", "nphj_build", "nphj_probe",
     "hgb_group_id", "hgb_aggregate", "pgb", "sgb_reduce", "agg_init", "fused_probe", "group_emit",
-    "batch", "mlp"};
+    "batch", "mlp", "smj_merge"};
 
 }  // namespace
 

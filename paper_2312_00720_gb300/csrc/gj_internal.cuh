@@ -370,6 +370,7 @@ enum KernelKind {
   KK_GROUP_EMIT,
   KK_BATCH,
   KK_MLP,
+  KK_SMJ_MERGE,
   KK_COUNT
 };
 // Brackets one kernel launch: counts it and, when timing is on, records CUDA

@@ -1191,7 +1191,7 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
       io.r_tid = (const int32_t*)rc.dst[0];
       io.s_tid = (const int32_t*)sc.dst[0];
     }
-    LaunchScope ls(ctx, KK_PHJ_PROBE);
+    LaunchScope ls(ctx, KK_SMJ_MERGE);
     smj_merge_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>(rk2, nr, sk2, ns, io, tstat, counter, ntiles,
                                                                ctx.d_status);
     return cuda_check(cudaGetLastError());
