@@ -302,3 +302,19 @@ def test_mlp_linear_special_case():
     y, _ = mlp.forward(mlp.pack(p), x)
     want = ((x @ p["w1"].T + 1) @ p["w2"].T + 1) @ p["w3"].T + p["b3"]
     assert np.allclose(y, want, rtol=1e-12)
+
+
+def test_many_to_many_generator_draws_from_nk_keys():
+    a = wl.mn_join_workload(5000, 7000, 300, 2, 1, seed=4)
+    b = wl.mn_join_workload(5000, 7000, 300, 2, 1, seed=4)
+    for k in ("rkey", "skey"):
+        assert np.array_equal(a[k], b[k])
+    keys = np.union1d(a["rkey"], a["skey"])
+    assert keys.size <= 300 and np.unique(a["rkey"]).size > 250
+    assert len(a["rcols"]) == 2 and len(a["scols"]) == 1 and a["scols"][0].shape == (7000,)
+    # |T| = sum over keys of (R rows with it) x (S rows with it)
+    t = oracle.join(a["rkey"], a["rcols"], a["skey"], a["scols"])
+    rk, rc = np.unique(a["rkey"], return_counts=True)
+    sk, sc = np.unique(a["skey"], return_counts=True)
+    common, ri, si = np.intersect1d(rk, sk, return_indices=True)
+    assert len(t) == int((rc[ri].astype(np.int64) * sc[si]).sum())
