@@ -175,7 +175,7 @@ def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20, cpu: bool
     return out
 
 
-def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True):
+def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 6784.5):
     """One query: |R| = 2^20 ⋈ |S| = 2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay), not materialised."""
     import torch
     w = wl.join_groupby_workload()
@@ -187,7 +187,10 @@ def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True):
         okeys, outs, ng = gj.join_groupby(*args, variant=v, sync=True)
         assert int(outs[1][: int(ng.item())].sum().item()) == 1 << 22
         ms = _event_ms(lambda: gj.join_groupby(*args, variant=v, sync=False), steps)
-        out[v] = {"us": ms * 1e3, "gtuples_s": ((1 << 20) + (1 << 22)) / (ms * 1e-3) / 1e9}
+        # minimal bytes: R (key + pay) and S (key + pay) read once, 1024 groups x 20 B written
+        min_bytes = ((1 << 20) + (1 << 22)) * 8 + 1024 * 20
+        out[v] = {"us": ms * 1e3, "gtuples_s": ((1 << 20) + (1 << 22)) / (ms * 1e-3) / 1e9,
+                  "min_bytes_frac": min_bytes / (ms * 1e-3) / 1e9 / peak}
     if cpu:
         out["cpu_baseline"] = oracle_sample(
             lambda o: o.join_groupby(w["rkey"], w["rcols"], w["skey"], w["scols"], g_side=0, g_col=0, g_mod=1024,
@@ -196,7 +199,7 @@ def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True):
     return out
 
 
-def bench_many_to_many(gj, wl, steps: int = 5):
+def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6784.5):
     """Many-to-many join (Sec. 5.1): |R| = |S| = 2^26, keys uniform from 2^25 keys,
     two int32 payloads per side; every (r, s) pair materialised (about 2^27 rows)."""
     import torch
@@ -216,10 +219,12 @@ def bench_many_to_many(gj, wl, steps: int = 5):
     ms = _event_ms(step, steps)
     return {"workload": "|R| = |S| = 2^26, keys uniform from 2^25 distinct keys, 2 int32 payloads per side, "
                         "NPHJ with key chains", "output_rows": m, "ms": ms,
-            "gtuples_s": 2 * n / (ms * 1e-3) / 1e9, "output_gb_s": m * 20 / (ms * 1e-3) / 1e9}
+            "gtuples_s": 2 * n / (ms * 1e-3) / 1e9, "output_gb_s": m * 20 / (ms * 1e-3) / 1e9,
+            # minimal bytes: both inputs (key + 2 payloads) read once, every output row written once
+            "min_bytes_frac": (2 * n * 12 + m * 20) / (ms * 1e-3) / 1e9 / peak}
 
 
-def bench_batch(gj, wl, steps: int = 5, cpu: bool = True):
+def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):
     """512 join + group-by instances: one persistent graph launch vs 512 sequential gj_join_groupby calls."""
     import torch
     ws = wl.batch_workload(512, seed=7)
@@ -257,6 +262,8 @@ def bench_batch(gj, wl, steps: int = 5, cpu: bool = True):
                         "GROUP BY R.p0 mod G (G log-uniform [2^2, 2^16]), COUNT, SUM(S.p0), SUM(S.p1), SUM(R.p1)",
             "rows": rows, "batched_ms": batched, "sequential_ms": seq, "speedup": seq / batched,
             "batched_gtuples_s": rows / (batched * 1e-3) / 1e9, "sequential_gtuples_s": rows / (seq * 1e-3) / 1e9,
+            # minimal bytes: every input row (key + 2 payloads) read once
+            "batched_min_bytes_frac": rows * 12 / (batched * 1e-3) / 1e9 / peak,
             "tuned_config": {"build_rows": cfg[0], "probe_rows": cfg[1], "lookahead": cfg[2], "blocks_per_sm": cfg[3]},
             "tune_and_capture_s": tune_s}
 
@@ -467,9 +474,9 @@ def main():
             del h_in, h_out
             cpu = not args.no_cpu_baseline
             out["groupby"] = bench_groupby(gj, wl, peak, cpu=cpu)
-            out["one_query"] = bench_one_query(gj, wl, cpu=cpu)
-            out["batched"] = bench_batch(gj, wl, cpu=cpu)
-            out["many_to_many"] = bench_many_to_many(gj, wl)
+            out["one_query"] = bench_one_query(gj, wl, cpu=cpu, peak=peak)
+            out["batched"] = bench_batch(gj, wl, cpu=cpu, peak=peak)
+            out["many_to_many"] = bench_many_to_many(gj, wl, peak=peak)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
