@@ -54,3 +54,55 @@ def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gj, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         gj.load()
+
+
+def _table(gj, n, ncols, key_type=0, col_type=0, fake=0x1000):
+    t = gj.Table()
+    t.key_type, t.ncols, t.n = key_type, ncols, n
+    t.key = fake if n else None
+    for c in range(ncols):
+        t.col_type[c] = col_type
+        t.cols[c] = fake + 64 * (c + 1) if n else None
+    return t
+
+
+def test_argument_checks_run_before_any_device_work(lib):
+    """Invalid arguments are rejected on the host (GJ_ERR_INVALID_ARG = 1,
+    GJ_ERR_UNSUPPORTED = 2) before any CUDA call, so these run without a GPU.
+    The pointers are never dereferenced."""
+    from paper_2312_00720_gb300 import gj
+    R, S = _table(gj, 10, 1), _table(gj, 20, 1)
+    T = _table(gj, 20, 2)
+    cnt = ctypes.c_void_p(0x2000)
+    o = gj.Options()
+    lib.gj_options_default(ctypes.byref(o))
+    join = lambda R, S, o, T, cap: lib.gj_join(ctypes.byref(R), ctypes.byref(S), ctypes.byref(o), ctypes.byref(T),
+                                                ctypes.c_int64(cap), cnt, None)
+    o.join_variant = 7  # past GJ_JOIN_SMJ_UR
+    assert join(R, S, o, T, 20) == 1
+    lib.gj_options_default(ctypes.byref(o))
+    o.radix_bits = 17
+    assert join(R, S, o, T, 20) == 1
+    lib.gj_options_default(ctypes.byref(o))
+    assert join(R, _table(gj, 20, 1, key_type=1), o, T, 20) == 1  # key types differ
+    assert join(R, S, o, _table(gj, 20, 3), 20) == 1  # T has the wrong column count
+    assert join(R, S, o, T, -1) == 1
+    assert join(_table(gj, 1 << 31, 1), S, o, T, 20) == 2  # more rows than supported
+
+    ops = (ctypes.c_int32 * 2)(0, 1)
+    cols = (ctypes.c_int32 * 2)(0, 0)
+    outs = (ctypes.c_void_p * 2)(0x3000, 0x4000)
+    gb = lambda t, nagg, ops, o: lib.gj_groupby(ctypes.byref(t), nagg, ops, cols, ctypes.byref(o),
+                                                 ctypes.c_void_p(0x5000), outs, ctypes.c_int64(8), cnt, None)
+    o.groupby_variant = 7  # past GJ_GB_SGB_DE
+    assert gb(R, 2, ops, o) == 1
+    lib.gj_options_default(ctypes.byref(o))
+    assert gb(R, 0, ops, o) == 1
+    assert gb(R, 2, (ctypes.c_int32 * 2)(0, 9), o) == 1  # unknown aggregate
+    assert lib.gj_groupby(ctypes.byref(R), 2, (ctypes.c_int32 * 2)(0, 0), (ctypes.c_int32 * 2)(0, 3),
+                          ctypes.byref(o), ctypes.c_void_p(0x5000), outs, ctypes.c_int64(8), cnt, None) == 1
+
+    # the allocation-free partition: more than 8 bits in its one pass is unsupported
+    out = _table(gj, 10, 1)
+    assert lib.gj_radix_partition_noalloc(ctypes.byref(R), 0, 9, 0, ctypes.byref(out), None, 0, None) == 2
+    assert lib.gj_radix_partition_noalloc(ctypes.byref(R), 4, 4, 0, ctypes.byref(out), None, 0, None) == 1
