@@ -211,17 +211,21 @@ def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6784.5):
     tkey = torch.empty(cap, dtype=torch.int32, device="cuda")
     tcols = [torch.empty(cap, dtype=torch.int32, device="cuda") for _ in range(4)]
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    step = lambda: gj.join(rk, rc, sk, sc, variant="nphj_mn", capacity=cap, sync=False, out=(tkey, tcols), count=cnt)
-    step()
-    torch.cuda.synchronize()
-    assert gj.device_status() == 0
-    m = int(cnt.item())
-    ms = _event_ms(step, steps)
-    return {"workload": "|R| = |S| = 2^26, keys uniform from 2^25 distinct keys, 2 int32 payloads per side, "
-                        "NPHJ with key chains", "output_rows": m, "ms": ms,
-            "gtuples_s": 2 * n / (ms * 1e-3) / 1e9, "output_gb_s": m * 20 / (ms * 1e-3) / 1e9,
-            # minimal bytes: both inputs (key + 2 payloads) read once, every output row written once
-            "min_bytes_frac": (2 * n * 12 + m * 20) / (ms * 1e-3) / 1e9 / peak}
+    out = {"workload": "|R| = |S| = 2^26, keys uniform from 2^25 distinct keys, 2 int32 payloads per side; "
+                       "nphj_mn: global table with key chains, phj_mn: GFTR partitions with a partition-"
+                       "clustered table"}
+    for v in ("nphj_mn", "phj_mn"):
+        step = lambda: gj.join(rk, rc, sk, sc, variant=v, capacity=cap, sync=False, out=(tkey, tcols), count=cnt)
+        step()
+        torch.cuda.synchronize()
+        assert gj.device_status() == 0
+        m = int(cnt.item())
+        ms = _event_ms(step, steps)
+        out["output_rows"] = m
+        out[v] = {"ms": ms, "gtuples_s": 2 * n / (ms * 1e-3) / 1e9, "output_gb_s": m * 20 / (ms * 1e-3) / 1e9,
+                  # minimal bytes: both inputs (key + 2 payloads) read once, every output row written once
+                  "min_bytes_frac": (2 * n * 12 + m * 20) / (ms * 1e-3) / 1e9 / peak}
+    return out
 
 
 def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):

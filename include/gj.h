@@ -83,7 +83,10 @@ typedef enum {
                          gj_join only; never chosen by AUTO */
   GJ_JOIN_SMJ_TR = 5, /* sort-merge join: both sides radix-sorted on the whole key with their payloads,
                          tiles of S merged against their range of R (merge path), Sec. 3.1.1 */
-  GJ_JOIN_SMJ_UR = 6  /* the same with (key, tuple id) sorted and payloads gathered by id (GFUR) */
+  GJ_JOIN_SMJ_UR = 6, /* the same with (key, tuple id) sorted and payloads gathered by id (GFUR) */
+  GJ_JOIN_PHJ_MN = 7  /* many-to-many with GFTR: R and S radix-partitioned with their payloads, a global
+                         table whose slots cluster each partition's keys, key chains inside partitions
+                         (Sec. 5.1); gj_join only; never chosen by AUTO */
 } gj_join_variant;
 
 typedef enum {

@@ -262,7 +262,7 @@ gj_status gj_join(const gj_table* R, const gj_table* S, const gj_options* opt, g
   gj_options defaults;
   gj_options_default(&defaults);
   if (!opt) opt = &defaults;
-  if (opt->join_variant < GJ_JOIN_AUTO || opt->join_variant > GJ_JOIN_SMJ_UR) return GJ_ERR_INVALID_ARG;
+  if (opt->join_variant < GJ_JOIN_AUTO || opt->join_variant > GJ_JOIN_PHJ_MN) return GJ_ERR_INVALID_ARG;
   if (opt->radix_bits < 0 || opt->radix_bits > 16 || opt->bits_per_pass < 0 || opt->bits_per_pass > 8)
     return GJ_ERR_INVALID_ARG;
   Ctx ctx;

@@ -767,19 +767,33 @@ __global__ void __launch_bounds__(kThreads) smj_merge_kernel(const K* __restrict
   emit_tile<K>(tile, ntiles, tile_base, tile_n, s_key, s_midx, s_pos, io, tile_status, err, s_scan, &s_base);
 }
 
-// ---------------------------------------------------------------- NPHJ, many-to-many
+// ---------------------------------------------------------------- many-to-many
 // R.key may repeat (Sec. 5.1, many-to-many joins). The global table keeps, per
 // key, the last R row inserted (row + 1); next[r] links each R row to the one
 // inserted before it with the same key (-1 ends the chain), so the rows of a key
 // are one chain. Chain order follows the insertions and is not fixed, which only
 // reorders T.
+//
+// Non-partitioned (NPHJ-MN) the table is indexed by the key's hash. Partitioned
+// (PHJ-MN, GFTR: R and S radix-partitioned on the low cbits hash bits with their
+// payloads) the slot puts the partition id in the top cbits of the slot index, so
+// the keys of one partition occupy one contiguous stretch of the table: probe
+// rows taken in S' order stay inside a few KB of it, and a key's chain of R' rows
+// lies inside its partition.
+__device__ __forceinline__ uint64_t mn_slot(uint64_t h, uint64_t mask, int cbits, int logslots) {
+  if (cbits == 0) return h & mask;
+  const uint64_t p = h & ((uint64_t(1) << cbits) - 1);
+  const uint64_t rest = (h >> cbits) & ((uint64_t(1) << (logslots - cbits)) - 1);
+  return (p << (logslots - cbits)) | rest;
+}
+
 template <typename K>
 __global__ void nphj_mn_build_kernel(const K* __restrict__ rkey, int64_t nr, int32_t* __restrict__ ht, uint64_t mask,
-                                     int32_t* __restrict__ next, int* err) {
+                                     int cbits, int logslots, int32_t* __restrict__ next, int* err) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
     const K k = rkey[i];
-    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    uint64_t sl = mn_slot(KeyTraits<K>::hash64(k), mask, cbits, logslots);
     bool done = false;
     for (uint64_t probe = 0; probe <= mask; ++probe) {
       const int prev = atomicCAS(&ht[sl], 0, (int)(i + 1));
@@ -807,6 +821,7 @@ __global__ void nphj_mn_build_kernel(const K* __restrict__ rkey, int64_t nr, int
 template <typename K>
 __global__ void __launch_bounds__(kThreads) nphj_mn_probe_kernel(const K* __restrict__ rkey,
                                                                  const int32_t* __restrict__ ht, uint64_t mask,
+                                                                 int cbits, int logslots,
                                                                  const int32_t* __restrict__ next,
                                                                  const K* __restrict__ skey, int64_t ns, JoinIO io,
                                                                  uint64_t* tile_status, int* tile_counter,
@@ -829,7 +844,7 @@ __global__ void __launch_bounds__(kThreads) nphj_mn_probe_kernel(const K* __rest
     cnt[j] = 0;
     if (i >= ns) continue;
     const K k = skey[i];
-    uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+    uint64_t sl = mn_slot(KeyTraits<K>::hash64(k), mask, cbits, logslots);
     for (uint64_t probe = 0; probe <= mask; ++probe) {
       const int v = __ldg(ht + sl);
       if (v == 0) break;
@@ -1197,24 +1212,58 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
     return cuda_check(cudaGetLastError());
   }
 
-  if (variant == GJ_JOIN_NPHJ_MN) {
+  if (variant == GJ_JOIN_NPHJ_MN || variant == GJ_JOIN_PHJ_MN) {
+    const K* rk = (const K*)R->key;
+    const K* sk = (const K*)S->key;
+    for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
+    for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
+    int cbits = 0;
+    if (variant == GJ_JOIN_PHJ_MN && bits > 0) {
+      // GFTR: both sides partitioned on the low hash bits with their payloads
+      K* rk2 = scr.get_as<K>(nr);
+      K* sk2 = scr.get_as<K>(ns);
+      ColSet rc{}, sc{};
+      rc.n = R->ncols;
+      for (int c = 0; c < R->ncols; ++c) {
+        rc.src[c] = R->cols[c];
+        rc.size[c] = dtype_size(R->col_type[c]);
+        rc.dst[c] = scr.get((size_t)nr * rc.size[c]);
+      }
+      sc.n = S->ncols;
+      for (int c = 0; c < S->ncols; ++c) {
+        sc.src[c] = S->cols[c];
+        sc.size[c] = dtype_size(S->col_type[c]);
+        sc.dst[c] = scr.get((size_t)ns * sc.size[c]);
+      }
+      if (scr.failed()) return GJ_ERR_OOM;
+      const int kt = sizeof(K) == 8 ? GJ_I64 : GJ_I32;
+      if ((st = radix_partition_run(ctx, scr, kt, rk, rk2, rc, nr, 0, bits, kHashed, bpp)) != GJ_OK) return st;
+      if ((st = radix_partition_run(ctx, scr, kt, sk, sk2, sc, ns, 0, bits, kHashed, bpp)) != GJ_OK) return st;
+      rk = rk2;
+      sk = sk2;
+      for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = rc.dst[c];
+      for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = sc.dst[c];
+      cbits = bits;
+    }
     uint64_t slots = 1;
-    while (slots < (uint64_t)std::max<int64_t>(2 * nr, 2)) slots <<= 1;
+    int logslots = 0;
+    while (slots < (uint64_t)std::max<int64_t>(2 * nr, 2)) {
+      slots <<= 1;
+      ++logslots;
+    }
+    if (cbits > logslots) cbits = 0;  // more partitions than slots: plain hashing
     int32_t* ht = scr.get_as<int32_t>(slots);
     int32_t* next = scr.get_as<int32_t>(std::max<int64_t>(nr, 1));
     if (scr.failed()) return GJ_ERR_OOM;
     if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
-    for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
-    for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
     {
       int blocks = (int)std::min<int64_t>((nr + 255) / 256, (int64_t)ctx.num_sms * 16);
       LaunchScope ls(ctx, KK_NPHJ_BUILD);
-      nphj_mn_build_kernel<K><<<blocks, 256, 0, s>>>((const K*)R->key, nr, ht, slots - 1, next, ctx.d_status);
+      nphj_mn_build_kernel<K><<<blocks, 256, 0, s>>>(rk, nr, ht, slots - 1, cbits, logslots, next, ctx.d_status);
     }
     LaunchScope ls(ctx, KK_NPHJ_PROBE);
-    nphj_mn_probe_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>((const K*)R->key, ht, slots - 1, next,
-                                                                   (const K*)S->key, ns, io, tstat, counter, ntiles,
-                                                                   ctx.d_status);
+    nphj_mn_probe_kernel<K><<<(unsigned)ntiles, kThreads, 0, s>>>(rk, ht, slots - 1, cbits, logslots, next, sk, ns,
+                                                                   io, tstat, counter, ntiles, ctx.d_status);
     return cuda_check(cudaGetLastError());
   }
 

@@ -19,7 +19,7 @@ MAX_COLS = 8
 MAX_AGGS = 32
 I32, I64 = 0, 1
 AGG = {"sum": 0, "count": 1, "min": 2, "max": 3}
-JOIN = {"auto": 0, "phj_tr": 1, "phj_ur": 2, "nphj": 3, "nphj_mn": 4, "smj_tr": 5, "smj_ur": 6}
+JOIN = {"auto": 0, "phj_tr": 1, "phj_ur": 2, "nphj": 3, "nphj_mn": 4, "smj_tr": 5, "smj_ur": 6, "phj_mn": 7}
 GROUPBY = {"auto": 0, "hgb": 1, "sgb": 2, "pgb": 3, "sgb_ur": 4, "pgb_ur": 5, "sgb_de": 6}
 STATUS = {0: "GJ_OK", 1: "GJ_ERR_INVALID_ARG", 2: "GJ_ERR_UNSUPPORTED", 3: "GJ_ERR_OOM", 4: "GJ_ERR_CAPACITY",
           5: "GJ_ERR_DUPLICATE_KEY", 6: "GJ_ERR_TIMEOUT", 7: "GJ_ERR_CUDA"}

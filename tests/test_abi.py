@@ -78,7 +78,7 @@ def test_argument_checks_run_before_any_device_work(lib):
     lib.gj_options_default(ctypes.byref(o))
     join = lambda R, S, o, T, cap: lib.gj_join(ctypes.byref(R), ctypes.byref(S), ctypes.byref(o), ctypes.byref(T),
                                                 ctypes.c_int64(cap), cnt, None)
-    o.join_variant = 7  # past GJ_JOIN_SMJ_UR
+    o.join_variant = 8  # past GJ_JOIN_PHJ_MN
     assert join(R, S, o, T, 20) == 1
     lib.gj_options_default(ctypes.byref(o))
     o.radix_bits = 17

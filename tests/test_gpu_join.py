@@ -140,26 +140,38 @@ def test_full_size_plain_join(gj, theta, mr, variant):
 @pytest.mark.parametrize("nr,ns,nk,ncr,ncs", [
     (1, 1, 1, 1, 1), (100, 100, 1, 2, 2), (1000, 3000, 50, 2, 2), (20011, 30011, 5000, 2, 2),
     (65536, 65536, 1 << 13, 2, 2), (100000, 70000, 100000, 3, 1), (5000, 4000, 4000, 0, 0)])
-def test_many_to_many_matches_oracle(gj, nr, ns, nk, ncr, ncs):
+@pytest.mark.parametrize("variant", ["nphj_mn", "phj_mn"])
+def test_many_to_many_matches_oracle(gj, variant, nr, ns, nk, ncr, ncs):
     w = wl.mn_join_workload(nr, ns, nk, ncr, ncs, seed=nr + nk)
     want = oracle.canonical(oracle_rows(w))
-    got = oracle.canonical(run_join(gj, w, "nphj_mn", capacity=max(1, want.shape[0])))
+    got = oracle.canonical(run_join(gj, w, variant, capacity=max(1, want.shape[0])))
     assert got.shape == want.shape
     assert np.array_equal(got, want)
 
 
-def test_many_to_many_int64_keys_and_pk_fk_input(gj):
+@pytest.mark.parametrize("variant", ["nphj_mn", "phj_mn"])
+def test_many_to_many_int64_keys_and_pk_fk_input(gj, variant):
     # 8-byte keys; and on a key-foreign-key input the pairs equal the FK-PK join's
     w = wl.mn_join_workload(30000, 40000, 7000, 2, 2, key_dtype=np.int64, seed=5)
     want = oracle.canonical(oracle_rows(w))
-    assert np.array_equal(oracle.canonical(run_join(gj, w, "nphj_mn", capacity=want.shape[0])), want)
+    assert np.array_equal(oracle.canonical(run_join(gj, w, variant, capacity=want.shape[0])), want)
     w = wl.join_workload(5000, 20011, 2, 2, mr=0.5, seed=3)
-    assert np.array_equal(oracle.canonical(run_join(gj, w, "nphj_mn")),
+    assert np.array_equal(oracle.canonical(run_join(gj, w, variant)),
                           oracle.canonical(run_join(gj, w, "nphj")))
 
 
-def test_many_to_many_capacity_overflow_is_reported(gj):
+def test_partitioned_many_to_many_with_few_partitions_or_hot_keys(gj):
+    # radix_bits 1: two partitions; nk = 3: three keys, each with thousands of rows
+    w = wl.mn_join_workload(20000, 300, 3, 1, 1, seed=6)
+    want = oracle.canonical(oracle_rows(w))
+    for bits in (1, 0):
+        got = oracle.canonical(run_join(gj, w, "phj_mn", capacity=want.shape[0], radix_bits=bits))
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", ["nphj_mn", "phj_mn"])
+def test_many_to_many_capacity_overflow_is_reported(gj, variant):
     w = wl.mn_join_workload(2000, 2000, 10, 1, 1, seed=8)  # about 4e5 pairs
     with pytest.raises(gj.GjError) as e:
-        run_join(gj, w, "nphj_mn", capacity=1000)
+        run_join(gj, w, variant, capacity=1000)
     assert e.value.code == 4
