@@ -283,6 +283,25 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time: every rank joins one MAX all-reduce (NCCL on the
+    GPU, gloo on the host)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gtuples(rows_per_rank: int, ms: float, world: int) -> float:
+    """Whole-job throughput: every rank processes rows_per_rank rows per step
+    (weak scaling); ms is the slowest rank's time per step."""
+    return world * rows_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -380,14 +399,10 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     assert gj.device_status() == 0
     ms_step = ms / args.steps
-    value = world * (NR + NS) / (ms_step * 1e-3) / 1e9
+    value = whole_job_gtuples(NR + NS, ms_step, world)
 
     # ---- per-kernel times on the launching stream (CUDA events around each launch)
     gj.profile_enable(True)
@@ -440,13 +455,9 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world)
     assert int(h_cnt.item()) == NS
-    e2e_value = world * (NR + NS) / (e2e_ms * 1e-3) / 1e9
+    e2e_value = whole_job_gtuples(NR + NS, e2e_ms, world)
 
     if rank == 0:
         out = {
