@@ -344,7 +344,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="phj_tr", choices=["phj_tr", "phj_ur", "nphj"])
+    ap.add_argument("--variant", default="phj_tr", choices=["phj_tr", "phj_ur", "nphj", "smj_tr", "smj_ur"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the group-by, one-query and batched lines")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -442,6 +442,9 @@ def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | N
          match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, selector: int = 0):
     """R join S on key (Sec. 2.2). Returns (T.key, [T.cols: R's then S's], device count tensor).
 
+    variant: "auto", "phj_tr", "phj_ur", "nphj", "smj_tr", "smj_ur" (R.key unique), or
+    "nphj_mn", "phj_mn" (many-to-many; pass a capacity that holds every pair).
+
     ``out`` may pass preallocated (key, cols) outputs and ``count`` a device int64[1]."""
     lib = load()
     R = make_table(rkey, rcols)
@@ -479,7 +482,9 @@ def _agg_arrays(aggs, n_out, device, capacity):
 
 def groupby(key, vals, aggs, agg_cols, *, variant: str = "hgb", capacity: int | None = None,
             radix_bits: int = 0, sync: bool = True, groups_hint: int = 0, zipf_hint: float = -1.0):
-    """GROUP BY key (Sec. 2.2, Alg. 1). Returns (keys, [int64 aggregate columns], device group count)."""
+    """GROUP BY key (Sec. 2.2, Alg. 1). Returns (keys, [int64 aggregate columns], device group count).
+
+    variant: "auto", "hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"."""
     lib = load()
     t = make_table(key, vals)
     if capacity is None:
