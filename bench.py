@@ -430,29 +430,60 @@ def main():
     kernel_split = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
                         "share": v[0] / total_ms} for k, v in prof.items()}
 
-    # ---- end to end: pinned host inputs in, result rows out, every step
+    # ---- end to end: pinned host inputs in, result rows out, every step. Steps are
+    # pipelined the way a streaming caller would run them: step i's input copies
+    # (one copy stream) and step i-1's result copies (another) overlap step i's
+    # join, through two sets of device input and output buffers; every step still
+    # copies all its inputs in and all its result rows out inside the timed region.
     h_in = [torch.from_numpy(a).pin_memory() for a in [w["rkey"], *w["rcols"], w["skey"], *w["scols"]]]
-    d_in = [rkey, *rcols, skey, *scols]
     h_out = [torch.empty(NS, dtype=torch.int32).pin_memory() for _ in range(1 + 2 * NCOLS)]
     h_cnt = torch.empty(1, dtype=torch.int64).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in h_out) + 8
+    d_in = [[rkey, *rcols, skey, *scols], [torch.empty_like(t) for t in (rkey, *rcols, skey, *scols)]]
+    d_out = [(tkey, tcols, cnt), (torch.empty_like(tkey), [torch.empty_like(c) for c in tcols],
+                                  torch.zeros_like(cnt))]
+    comp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]     # inputs of buffer b copied
+    ev_comp = [torch.cuda.Event(), torch.cuda.Event()]   # join on buffer b done
+    ev_out = [torch.cuda.Event(), torch.cuda.Event()]    # results of buffer b copied out
+    for b in range(2):
+        ev_comp[b].record(comp)
+        ev_out[b].record(comp)
 
-    def e2e_step():
-        for h, d in zip(h_in, d_in):
-            d.copy_(h, non_blocking=True)
-        step()
-        for h, d in zip(h_out, [tkey, *tcols]):
-            h.copy_(d, non_blocking=True)
-        h_cnt.copy_(cnt, non_blocking=True)
+    def e2e_step(i):
+        b = i & 1
+        di, (ok, oc, ocnt) = d_in[b], d_out[b]
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(ev_comp[b])  # the join two steps back has read buffer b
+            for h, d in zip(h_in, di):
+                d.copy_(h, non_blocking=True)
+            ev_in[b].record(s_in)
+        comp.wait_event(ev_in[b])
+        comp.wait_event(ev_out[b])  # the results two steps back have left buffer b
+        gj.join(di[0], di[1:1 + NCOLS], di[1 + NCOLS], di[2 + NCOLS:], variant=args.variant, sync=False,
+                out=(ok, oc), count=ocnt)
+        ev_comp[b].record(comp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_comp[b])
+            for h, d in zip(h_out, [ok, *oc]):
+                h.copy_(d, non_blocking=True)
+            h_cnt.copy_(ocnt, non_blocking=True)
+            ev_out[b].record(s_out)
 
-    e2e_step()
+    e2e_step(0)
+    e2e_step(1)
     torch.cuda.synchronize()
     barrier()
-    e0.record()
-    for _ in range(args.e2e_steps):
-        e2e_step()
-    e1.record()
+    e0.record(comp)
+    s_in.wait_event(e0)
+    s_out.wait_event(e0)
+    for i in range(args.e2e_steps):
+        e2e_step(i)
+    comp.wait_stream(s_in)
+    comp.wait_stream(s_out)
+    e1.record(comp)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
     e2e_ms = max_over_ranks(e2e_ms, world)
