@@ -106,3 +106,18 @@ def test_argument_checks_run_before_any_device_work(lib):
     out = _table(gj, 10, 1)
     assert lib.gj_radix_partition_noalloc(ctypes.byref(R), 0, 9, 0, ctypes.byref(out), None, 0, None) == 2
     assert lib.gj_radix_partition_noalloc(ctypes.byref(R), 4, 4, 0, ctypes.byref(out), None, 0, None) == 1
+
+
+def test_binding_variant_codes_match_the_header():
+    """The Python names of the join / group-by variants carry the enum values
+    include/gj.h declares."""
+    from paper_2312_00720_gb300 import gj
+    text = open(os.path.join(ROOT, "include", "gj.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    enum = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GJ_(?:JOIN|GB)_\w+)\s*=\s*(\d+)", text)}
+    for name, code in gj.JOIN.items():
+        assert enum["GJ_JOIN_" + name.upper()] == code, name
+    for name, code in gj.GROUPBY.items():
+        assert enum["GJ_GB_" + name.upper()] == code, name
+    assert len([k for k in enum if k.startswith("GJ_JOIN_")]) == len(gj.JOIN)
+    assert len([k for k in enum if k.startswith("GJ_GB_")]) == len(gj.GROUPBY)
