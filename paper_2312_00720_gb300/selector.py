@@ -6,7 +6,7 @@ PGB) of a query; the selector takes the argmin within each family. Training data
 are timings the library itself produces on a seeded grid of synthetic queries;
 training runs on the GPU through the library's own forward, backward and Adam
 kernels (gj_mlp_*). The paper's rules (gj_heuristic_choose) are the fallback and
-the comparison point; exhaustive timing of every variant is the judge (regret).
+the comparison point; exhaustive timing of every variant is the yardstick (regret).
 
 Inputs of the sweep are generated on the device with torch's random generators:
 they only need the workload's shape (sizes, key width, skew, match ratio, group
