@@ -107,14 +107,23 @@ __global__ void __launch_bounds__(256) hgb_group_id_kernel(const K* __restrict__
   }
 }
 
-// out[j][0..g) = identity of op j, g read from the device counter.
+// out[j][0..g) = the starting value of aggregate j, g read from the device
+// counter. MIN/MAX over a 4-byte column start at the 32-bit identity
+// (INT32_MAX / INT32_MIN): every group holds at least one row, whose value fits
+// 32 bits, so the result is unchanged, and a block's shared-memory slot still at
+// that identity has nothing to add (it may hold a real INT32_MAX, which then is
+// already the starting value).
 __global__ void agg_init_kernel(Aggs A, const int64_t* __restrict__ ngroups, int64_t cap) {
   const int64_t g = min64(*ngroups, cap);
   const int64_t total = g * A.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
-    int j = (int)(t / g);
-    A.out[j][t - (int64_t)j * g] = agg_identity(A.op[j]);
+    const int j = (int)(t / g);
+    const int op = A.op[j];
+    int64_t v = agg_identity(op);
+    if (A.size[j] == 4 && op == GJ_AGG_MIN) v = INT32_MAX;
+    if (A.size[j] == 4 && op == GJ_AGG_MAX) v = INT32_MIN;
+    A.out[j][t - (int64_t)j * g] = v;
   }
 }
 

@@ -114,3 +114,19 @@ def test_full_size_plain_groupby(gj, g, kdt, theta):
     for v in VARIANTS:
         got = oracle.canonical(run_gb(gj, w["key"], w["vals"], AGGS, COLS, v))
         assert np.array_equal(got, want), v
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_extreme_int32_values(gj, variant):
+    # groups whose values all sit at INT32_MAX / INT32_MIN: the 32-bit identities of
+    # MIN / MAX are real values here and must come out as such
+    rng = np.random.default_rng(17)
+    n = 40000
+    key = rng.integers(0, 64, n).astype(np.int32)
+    v = rng.integers(-5, 5, n).astype(np.int32)
+    v[key < 8] = np.iinfo(np.int32).max
+    v[(key >= 8) & (key < 16)] = np.iinfo(np.int32).min
+    aggs = ["min", "max", "sum", "count"]
+    cols = [0, 0, 0, 0]
+    got = oracle.canonical(run_gb(gj, key, [v], aggs, cols, variant))
+    assert np.array_equal(got, want_rows(key, [v], aggs, cols))
