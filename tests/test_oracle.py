@@ -318,3 +318,28 @@ def test_many_to_many_generator_draws_from_nk_keys():
     sk, sc = np.unique(a["skey"], return_counts=True)
     common, ri, si = np.intersect1d(rk, sk, return_indices=True)
     assert len(t) == int((rc[ri].astype(np.int64) * sc[si]).sum())
+
+
+@pytest.mark.parametrize("n,g,theta", [(1 << 20, 1 << 20, 0.0), (1 << 21, 1 << 12, 0.0), (1 << 20, 1 << 22, 0.0),
+                                       (1 << 20, 1 << 18, 1.0)])
+def test_groupby_generator_distinct_count(n, g, theta):
+    # n draws over g ids: E[distinct] = sum_r 1 - (1 - p_r)^n, which for the uniform law
+    # is g (1 - (1 - 1/g)^n) ~ g (1 - e^{-n/g}); occupancy indicators are negatively
+    # associated, so Var[distinct] <= sum_r q_r (1 - q_r) with q_r = 1 - (1 - p_r)^n
+    w = wl.groupby_workload(n, g, nvals=1, theta=theta, seed=21)
+    p = np.arange(1, g + 1, dtype=np.float64) ** -theta
+    p /= p.sum()
+    q = -np.expm1(n * np.log1p(-p))
+    mean, sd = q.sum(), math.sqrt(float(np.sum(q * (1.0 - q))))
+    got = np.unique(w["key"]).size
+    assert abs(got - mean) <= 6.0 * sd + 1.0
+    if theta == 0.0:
+        assert mean == pytest.approx(g * (1.0 - math.exp(-n / g)), rel=1e-5)
+        assert w["key"].min() >= 0 and w["key"].max() < g
+    # 8-byte keys come from a bijection of the same ids: the same groups, the same sizes
+    w8 = wl.groupby_workload(n, g, nvals=1, theta=theta, seed=21, key_dtype=np.int64)
+    _, c4 = np.unique(w["key"], return_counts=True)
+    _, c8 = np.unique(w8["key"], return_counts=True)
+    assert np.array_equal(np.sort(c4), np.sort(c8))
+    assert np.array_equal(w["vals"][0], w8["vals"][0])
+    assert w["vals"][0].min() >= -(2**20) and w["vals"][0].max() < 2**20
