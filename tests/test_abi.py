@@ -121,3 +121,21 @@ def test_binding_variant_codes_match_the_header():
         assert enum["GJ_GB_" + name.upper()] == code, name
     assert len([k for k in enum if k.startswith("GJ_JOIN_")]) == len(gj.JOIN)
     assert len([k for k in enum if k.startswith("GJ_GB_")]) == len(gj.GROUPBY)
+
+
+def test_heuristic_choice_matches_the_oracle_rules(lib):
+    """The library's rule-based variant choice (gj_heuristic_choose, host code)
+    agrees with the oracle's statement of the paper's join rule and group-by
+    decision tree over a grid of hints. The library sizes HGB's shared memory
+    as 8 bytes per aggregate under a 200 KB budget when the device does not
+    report a smaller one."""
+    import itertools
+    from oracle import heuristics as hz
+    from paper_2312_00720_gb300 import gj
+    jcode = {hz.JOIN_PHJ_TR: gj.JOIN["phj_tr"], hz.JOIN_PHJ_UR: gj.JOIN["phj_ur"]}
+    gcode = {hz.GB_HGB: gj.GROUPBY["hgb"], hz.GB_SGB: gj.GROUPBY["sgb"], hz.GB_PGB: gj.GROUPBY["pgb"]}
+    for mr, z, kb, groups, nagg in itertools.product((0.1, 0.24, 0.25, 1.0), (0.0, 0.49, 0.5, 1.0, 1.25), (4, 8),
+                                                     (4, 2560, 2561, 1 << 20), (1, 10)):
+        jv, gv = gj.heuristic_choose(1 << 20, 1 << 22, kb, 2, 2, nagg, z, mr, groups)
+        assert jv == jcode[hz.choose_join(mr, z, kb)], (mr, z, kb)
+        assert gv == gcode[hz.choose_groupby(groups, 8 * nagg, 200 * 1024, z, kb)], (groups, nagg, z)
