@@ -139,3 +139,15 @@ def test_heuristic_choice_matches_the_oracle_rules(lib):
         jv, gv = gj.heuristic_choose(1 << 20, 1 << 22, kb, 2, 2, nagg, z, mr, groups)
         assert jv == jcode[hz.choose_join(mr, z, kb)], (mr, z, kb)
         assert gv == gcode[hz.choose_groupby(groups, 8 * nagg, 200 * 1024, z, kb)], (groups, nagg, z)
+
+
+def test_query_features_follow_the_header(lib):
+    """gj_query_features (host code) writes the 12 raw features include/gj.h lists."""
+    import math
+    from paper_2312_00720_gb300 import gj
+    for nr, ns, kb, cr, cs, nagg, z, mr, g in [(1 << 20, 1 << 22, 4, 2, 3, 4, 0.5, 0.25, 1 << 12),
+                                               (1000, 10, 8, 1, 8, 10, 0.0, 1.0, 7), (0, 5, 4, 1, 1, 1, 1.25, 0.1, 1)]:
+        f = gj.query_features(nr, ns, kb, cr, cs, nagg, z, mr, g)
+        want = [math.log2(nr + 1), math.log2(ns + 1), kb, cr, cs, z, mr, math.log2(g + 1), nagg,
+                math.log2((nr + 1) / (ns + 1)), 4 * cs, math.log2(g + 1) / math.log2(ns + 2)]
+        assert f.tolist() == pytest.approx(want, rel=1e-6, abs=1e-6)
