@@ -338,6 +338,33 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": "Gtuples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def groupby_case(spec: str):
+    """One call per listed group-by variant, synchronised, on seeded input: n =
+    2^LOG2N int32 keys over 2^LOG2G ids, three int32 values, COUNT + SUM/MIN/MAX
+    per column. Prints one JSON line; no timing (run under a profiler)."""
+    import torch
+
+    from paper_2312_00720_gb300 import gj
+    from paper_2312_00720_gb300 import workloads as wl
+
+    parts = spec.split(",")
+    lgn, lgg, variants = int(parts[0]), int(parts[1]), parts[2:]
+    gj.load()
+    w = wl.groupby_workload(1 << lgn, 1 << lgg, nvals=3, seed=77)
+    key = torch.from_numpy(w["key"]).cuda()
+    vals = [torch.from_numpy(v).cuda() for v in w["vals"]]
+    aggs = ["count"] + ["sum", "min", "max"] * 3
+    cols = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
+    groups = {}
+    for v in variants:
+        _, _, ng = gj.groupby(key, vals, aggs, cols, variant=v, sync=True)
+        groups[v] = int(ng.item())
+    torch.cuda.synchronize()
+    if gj.device_status() != 0:
+        raise RuntimeError("device error in the group-by case")
+    print(json.dumps({"groupby_case": {"n": 1 << lgn, "ids": 1 << lgg, "groups": groups}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,7 +376,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the group-by, one-query and batched lines")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--scale", type=int, default=0, help="divide |R| and |S| by 2^scale (profiling captures only)")
+    ap.add_argument("--groupby-case", default=None, metavar="LOG2N,LOG2G,VARIANT[,VARIANT..]",
+                    help="run each group-by variant once on 2^LOG2N rows over 2^LOG2G ids and exit "
+                         "(the small case the group-by kernel captures are taken on)")
     args = ap.parse_args()
+    if args.groupby_case:
+        groupby_case(args.groupby_case)
+        return
     global NR, NS, MIN_BYTES
     NR, NS = NR >> args.scale, NS >> args.scale
     MIN_BYTES = (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES
