@@ -130,17 +130,23 @@ def join_groupby_workload(nr: int = 1 << 20, ns: int = 1 << 22, seed: int = 5):
     return join_workload(nr, ns, 1, 1, theta=0.0, mr=1.0, seed=seed)
 
 
+def batch_sizes(nq: int = 512, *, log_r_lo: float = 10.0, log_r_hi: float = 20.0,
+                log_g_lo: float = 2.0, log_g_hi: float = 16.0, seed: int = 7):
+    """(|R|, group modulus) of each batched instance: both log-uniform."""
+    rng = _rng(seed, 0)
+    lr = rng.uniform(log_r_lo, log_r_hi, size=nq)
+    lg = rng.uniform(log_g_lo, log_g_hi, size=nq)
+    return [(int(round(2.0 ** a)), int(round(2.0 ** b))) for a, b in zip(lr, lg)]
+
+
 def batch_workload(nq: int = 512, *, log_r_lo: float = 10.0, log_r_hi: float = 20.0,
                    log_g_lo: float = 2.0, log_g_hi: float = 16.0, s_factor: int = 4, seed: int = 7):
     """Instances for the batched path: |R| log-uniform, |S| = s_factor |R|, uniform FK,
     two int32 payloads per side, group cardinality log-uniform (returned as the modulus)."""
-    rng = _rng(seed, 0)
-    lr = rng.uniform(log_r_lo, log_r_hi, size=nq)
-    lg = rng.uniform(log_g_lo, log_g_hi, size=nq)
     out = []
-    for i in range(nq):
-        nr = int(round(2.0 ** lr[i]))
+    sizes = batch_sizes(nq, log_r_lo=log_r_lo, log_r_hi=log_r_hi, log_g_lo=log_g_lo, log_g_hi=log_g_hi, seed=seed)
+    for i, (nr, modulus) in enumerate(sizes):
         w = join_workload(nr, s_factor * nr, 2, 2, seed=seed * 100003 + i)
-        w["modulus"] = int(round(2.0 ** lg[i]))
+        w["modulus"] = modulus
         out.append(w)
     return out

@@ -343,3 +343,21 @@ def test_groupby_generator_distinct_count(n, g, theta):
     assert np.array_equal(np.sort(c4), np.sort(c8))
     assert np.array_equal(w["vals"][0], w8["vals"][0])
     assert w["vals"][0].min() >= -(2**20) and w["vals"][0].max() < 2**20
+
+
+def test_batch_generator_sizes_follow_the_log_uniform_law():
+    # log2 |R| ~ U[10, 20] and log2 G ~ U[2, 16] over 512 instances: a Kolmogorov-Smirnov
+    # bound on each, and the mean |R| against E[2^U] = (2^20 - 2^10) / (10 ln 2)
+    sizes = wl.batch_sizes(512)
+    nr = np.array([a for a, _ in sizes], dtype=np.float64)
+    g = np.array([b for _, b in sizes], dtype=np.float64)
+    assert nr.min() >= 2**10 and nr.max() <= 2**20 and g.min() >= 4 and g.max() <= 2**16
+    for x, lo, hi in ((np.log2(nr), 10.0, 20.0), (np.log2(g), 2.0, 16.0)):
+        u = np.sort((x - lo) / (hi - lo))
+        k = np.arange(1, len(u) + 1) / len(u)
+        d = max(np.max(k - u), np.max(u - (k - 1.0 / len(u))))
+        assert d < 1.95 / math.sqrt(len(u)) + 0.5 / len(u)   # 99.9 % quantile, plus rounding to integers
+    mean = (2.0**20 - 2.0**10) / (10 * math.log(2))
+    var = (4.0**20 - 4.0**10) / (10 * math.log(4)) - mean**2
+    assert abs(nr.mean() - mean) < 5 * math.sqrt(var / len(nr))
+    assert round(mean, -3) == 151000   # E[|R|] of the batched configuration, about 1.51e5
