@@ -16,6 +16,8 @@
 // (each is bounded anyway). Each query computes what gj_join_groupby computes
 // with the non-partitioned table; the batch only removes per-query launches
 // and host round trips, and keeps a small query's table in L2 while it runs.
+// The paper has no batched mode: this is a scheduling layer over the group-by
+// that follows a join (Sec. 1) with the non-partitioned hash join of Sec. 3.1.3.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,5 +1,7 @@
 // Variant-selector network: hand-written FP32 forward, backward and optimiser
-// kernels, and the selector state used by the AUTO variants.
+// kernels, and the selector state used by the AUTO variants. Once installed, the
+// network stands in for the paper's variant rules (the join rule of Sec. 7 and
+// the group-by decision tree of Fig. groupby-dt), which stay the fallback.
 //
 // Forward: one block of 64 threads per sample, thread j owns hidden unit j of
 // both layers; the 6 outputs are reduced by threads 0..5. Backward: each block
