@@ -27,11 +27,12 @@
  *     call synchronises `stream` and returns that status, otherwise read it with
  *     gj_get_device_status. Kernels never trap.
  *   - Row counts are limited to 2^30 - 1 per input (GJ_ERR_UNSUPPORTED above).
- *   - Output row order is unspecified. PHJ-TR, PHJ-UR and SGB produce the same
- *     order on every run (stable partitioning, no atomics deciding positions);
- *     NPHJ, HGB and PGB assign positions through hash tables filled
- *     concurrently, so their row order may differ between runs while the result
- *     multiset does not.
+ *   - Output row order is unspecified. PHJ-TR, PHJ-UR, SMJ-TR, SMJ-UR, SGB-TR
+ *     and SGB-UR produce the same order on every run (stable partitioning, no
+ *     atomics deciding positions); NPHJ, the many-to-many joins, HGB, PGB and
+ *     SGB-DE assign positions or codes through hash tables filled concurrently,
+ *     so their row order may differ between runs while the result multiset does
+ *     not.
  */
 #ifndef GJ_H_
 #define GJ_H_
