@@ -178,8 +178,8 @@ gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_lo, int32_t
  * NPHJ, SMJ_TR, SMJ_UR and AUTO) R.key must be unique; a repeated key yields
  * GJ_ERR_DUPLICATE_KEY. NPHJ_MN and PHJ_MN join any R and S (many-to-many,
  * Sec. 5.1) and write every matching pair. R and S keys have the same type.
- * T has key_type = R.key_type, ncols = R.ncols + S.ncols with the R columns
- * first, column types as in the inputs. Rows beyond T_capacity are dropped with
+ * T has key_type = R.key_type, ncols = R.ncols + S.ncols (at most GJ_MAX_COLS,
+ * else GJ_ERR_INVALID_ARG) with the R columns first, column types as in the inputs. Rows beyond T_capacity are dropped with
  * GJ_ERR_CAPACITY; T_capacity >= S.n always suffices for a primary-key join.
  * *d_T_count (device int64) receives |T| (also when rows were dropped). */
 gj_status gj_join(const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,

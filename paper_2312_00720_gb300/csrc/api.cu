@@ -249,7 +249,7 @@ gj_status gj_join(const gj_table* R, const gj_table* S, const gj_options* opt, g
   if ((st = check_table(S, true)) != GJ_OK) return st;
   if (!T || !d_T_count || T_capacity < 0) return GJ_ERR_INVALID_ARG;
   if (R->key_type != S->key_type || T->key_type != R->key_type) return GJ_ERR_INVALID_ARG;
-  if (T->ncols != R->ncols + S->ncols) return GJ_ERR_INVALID_ARG;
+  if (T->ncols != R->ncols + S->ncols || T->ncols > GJ_MAX_COLS) return GJ_ERR_INVALID_ARG;
   for (int c = 0; c < R->ncols; ++c)
     if (T->col_type[c] != R->col_type[c]) return GJ_ERR_INVALID_ARG;
   for (int c = 0; c < S->ncols; ++c)

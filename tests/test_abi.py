@@ -86,6 +86,9 @@ def test_argument_checks_run_before_any_device_work(lib):
     lib.gj_options_default(ctypes.byref(o))
     assert join(R, _table(gj, 20, 1, key_type=1), o, T, 20) == 1  # key types differ
     assert join(R, S, o, _table(gj, 20, 3), 20) == 1  # T has the wrong column count
+    T9 = _table(gj, 20, 8)
+    T9.ncols = 9  # R.ncols + S.ncols = 9: more columns than a gj_table holds
+    assert join(_table(gj, 10, 5), _table(gj, 20, 4), o, T9, 20) == 1
     assert join(R, S, o, T, -1) == 1
     assert join(_table(gj, 1 << 31, 1), S, o, T, 20) == 2  # more rows than supported
 
