@@ -154,3 +154,19 @@ def test_query_features_follow_the_header(lib):
         want = [math.log2(nr + 1), math.log2(ns + 1), kb, cr, cs, z, mr, math.log2(g + 1), nagg,
                 math.log2((nr + 1) / (ns + 1)), 4 * cs, math.log2(g + 1) / math.log2(ns + 2)]
         assert f.tolist() == pytest.approx(want, rel=1e-6, abs=1e-6)
+
+
+def test_binding_refuses_host_tensors(lib):
+    """The binding has no CPU path: host tensors are refused before any library call."""
+    import torch
+    from paper_2312_00720_gb300 import gj
+    k = torch.arange(16, dtype=torch.int32)
+    v = [torch.zeros(16, dtype=torch.int32)]
+    with pytest.raises(ValueError, match="CUDA"):
+        gj.join(k, v, k, v, variant="phj_tr")
+    with pytest.raises(ValueError, match="CUDA"):
+        gj.groupby(k, v, ["count"], [0], variant="sgb")
+    with pytest.raises(ValueError, match="CUDA"):
+        gj.join_groupby(k, v, k, v, (0, 0, 4), ["count"], [(1, 0, 0)])
+    with pytest.raises(ValueError, match="CUDA"):
+        gj.radix_partition(k, v, 0, 4)
