@@ -128,7 +128,12 @@ def sweep(path: str, points, reps: int = 3, log=None) -> list:
                     done[r["point"]["id"]] = r
                 except (ValueError, KeyError):
                     continue
-    with open(path, "a") as f:
+    with open(path, "a+") as f:
+        # a sweep killed mid-write leaves a partial last line: start on a fresh one
+        if f.tell() > 0:
+            f.seek(f.tell() - 1)
+            if f.read(1) != "\n":
+                f.write("\n")
         for p in points:
             if p["id"] in done:
                 continue
