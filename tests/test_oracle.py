@@ -361,3 +361,17 @@ def test_batch_generator_sizes_follow_the_log_uniform_law():
     var = (4.0**20 - 4.0**10) / (10 * math.log(4)) - mean**2
     assert abs(nr.mean() - mean) < 5 * math.sqrt(var / len(nr))
     assert round(mean, -3) == 151000   # E[|R|] of the batched configuration, about 1.51e5
+
+
+def test_zipf_foreign_keys_follow_the_primary_key_order():
+    # S.key takes rank r to R.key[r] (R is a seeded permutation): R.key[0] is the
+    # hottest key with probability 1 / H_n, R.key[1] half of that, ...
+    nr, ns = 1000, 400000
+    w = wl.join_workload(nr, ns, 1, 1, theta=1.0, mr=1.0, seed=9)
+    p = 1.0 / np.arange(1, nr + 1)
+    p /= p.sum()
+    counts = {int(k): c for k, c in zip(*np.unique(w["skey"], return_counts=True))}
+    for r in (0, 1, 2, 9, 99):
+        want = ns * p[r]
+        assert abs(counts.get(int(w["rkey"][r]), 0) - want) < 5 * math.sqrt(want * (1 - p[r]))
+    assert set(counts) <= set(int(x) for x in w["rkey"])
