@@ -1,8 +1,9 @@
 """float64 reference of the variant-selector MLP -- TEST INFRASTRUCTURE ONLY.
 
 Network: x (12 features) -> Linear(12, 64) -> ReLU -> Linear(64, 64) -> ReLU ->
-Linear(64, 6); loss = mean over the batch of the mean over outputs with a target
-(mask = 1) of (y - t)^2. Weights are row-major [out][in]. This is the plain
+Linear(64, 6); loss = (1 / batch) * sum over samples and outputs of
+mask * (y - t)^2 (outputs without a target have mask 0). Weights are row-major
+[out][in]. This is the plain
 textbook definition of a two-hidden-layer perceptron with a masked squared
 error; the CUDA kernels are checked against it and it is checked against
 central finite differences.
