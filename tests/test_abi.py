@@ -170,3 +170,22 @@ def test_binding_refuses_host_tensors(lib):
         gj.join_groupby(k, v, k, v, (0, 0, 4), ["count"], [(1, 0, 0)])
     with pytest.raises(ValueError, match="CUDA"):
         gj.radix_partition(k, v, 0, 4)
+
+
+def test_selector_set_validates_on_the_host(lib):
+    """gj_selector_set copies host arrays; a missing normaliser or a non-positive
+    standard deviation is an argument error, NULL theta removes the network."""
+    import numpy as np
+    theta = np.zeros(5382, dtype=np.float32)
+    mean = np.zeros(12, dtype=np.float32)
+    std = np.ones(12, dtype=np.float32)
+    f = lib.gj_selector_set
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert f(theta.ctypes.data, None, std.ctypes.data) == 1
+    bad = std.copy()
+    bad[7] = 0.0
+    assert f(theta.ctypes.data, mean.ctypes.data, bad.ctypes.data) == 1
+    bad[7] = np.nan
+    assert f(theta.ctypes.data, mean.ctypes.data, bad.ctypes.data) == 1
+    assert f(theta.ctypes.data, mean.ctypes.data, std.ctypes.data) == 0
+    assert f(None, None, None) == 0
