@@ -200,7 +200,7 @@ def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 678
 
 
 def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6784.5):
-    """Many-to-many join (Sec. 5.1): |R| = |S| = 2^26, keys uniform from 2^25 keys,
+    """Many-to-many join (Sec. 5.1.9): |R| = |S| = 2^26, keys uniform from 2^25 keys,
     two int32 payloads per side; every (r, s) pair materialised (about 2^27 rows)."""
     import torch
     n, nk = 1 << 26, 1 << 25

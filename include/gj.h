@@ -79,7 +79,7 @@ typedef enum {
   GJ_JOIN_PHJ_TR = 1, /* radix-partitioned hash join, payloads partitioned with the keys (GFTR, Sec. 4.1.4) */
   GJ_JOIN_PHJ_UR = 2, /* same partitioning of (key, tuple id), payloads gathered by id (GFUR, Sec. 3.1.2, 4.1.4) */
   GJ_JOIN_NPHJ = 3,   /* non-partitioned hash join: global table on R, S probed in order (Sec. 3.1.3) */
-  GJ_JOIN_NPHJ_MN = 4, /* many-to-many (R.key need not be unique, Sec. 5.1): global table on R with a chain
+  GJ_JOIN_NPHJ_MN = 4, /* many-to-many (R.key need not be unique, Sec. 5.1.9): global table on R with a chain
                          of equal keys; every (r, s) pair is written, |T| = sum over S of its matches.
                          gj_join only; never chosen by AUTO */
   GJ_JOIN_SMJ_TR = 5, /* sort-merge join: both sides radix-sorted on the whole key with their payloads,
@@ -87,7 +87,7 @@ typedef enum {
   GJ_JOIN_SMJ_UR = 6, /* the same with (key, tuple id) sorted and payloads gathered by id (GFUR) */
   GJ_JOIN_PHJ_MN = 7  /* many-to-many with GFTR: R and S radix-partitioned with their payloads, a global
                          table whose slots cluster each partition's keys, key chains inside partitions
-                         (Sec. 5.1); gj_join only; never chosen by AUTO */
+                         (Sec. 5.1.9); gj_join only; never chosen by AUTO */
 } gj_join_variant;
 
 typedef enum {
@@ -98,7 +98,7 @@ typedef enum {
   GJ_GB_SGB_UR = 4, /* SGB with (key, tuple id) sorted and values gathered through the ids (GFUR, Sec. 4.1.2) */
   GJ_GB_PGB_UR = 5, /* PGB with (key, tuple id) partitioned and values gathered through the ids (GFUR) */
   GJ_GB_SGB_DE = 6  /* SGB on dictionary codes: dense group ids (HGB stage 1) sorted on ceil(log2 g) bits
-                       with the values, keys decoded from the dictionary (Sec. 4.1.3); synchronises the
+                       with the values, keys decoded from the dictionary (Sec. 4.4); synchronises the
                        stream once to read g */
 } gj_groupby_variant;
 
@@ -277,7 +277,7 @@ gj_status gj_batch_destroy(gj_batch_plan* plan);
  * A multi-layer perceptron x(12) -> 64 -> ReLU -> 64 -> ReLU -> y(6), FP32,
  * predicting log run time of the join variants PHJ-TR, PHJ-UR, NPHJ (y0..y2)
  * and the group-by variants HGB, SGB, PGB (y3..y5). The paper chooses variants
- * with cost models and heuristics (Sec. 4.1.3, 4.1.4, 4.4, 5.1.9, Fig.
+ * with cost models and heuristics (Sec. 4.1.3, 4.1.4, 4.4, 5.1.10, Fig.
  * groupby-dt); the network has no counterpart there and those rules remain the
  * fallback. Parameters are one float array of GJ_MLP_PARAMS values, row-major
  * [out][in] weights each followed by its bias: w1[64][12] b1[64] w2[64][64]

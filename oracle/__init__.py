@@ -10,7 +10,7 @@ Contents
     radix-partition permutation -- Sec. 2.2, 2.3 and Algorithm 1 of the paper.
   * ``cost_models``: the paper's cost models M2 (Sec. 4.1.3), M3 (Sec. 4.1.4)
     and M4 (Sec. 4.4), pinned to the printed "Estimated" series.
-  * ``heuristics``: the join rule of Sec. 5.1.9 / Sec. 7 and the group-by
+  * ``heuristics``: the join rule of Sec. 5.1.10 (join summary) / Sec. 7 and the group-by
     decision tree (Fig. groupby-dt).
   * ``mlp``: float64 forward/backward of the variant-selector network.
 

@@ -1,6 +1,6 @@
 """The paper's variant-choice rules -- TEST INFRASTRUCTURE ONLY.
 
-Join (Sec. 5.1.9 and Sec. 7): the GFTR partitioned hash join is preferred when
+Join (Sec. 5.1.10, the join summary, and Sec. 7): the GFTR partitioned hash join is preferred when
 the match ratio is at least 25 %, when the foreign keys are skewed, or when keys
 are 8 bytes; otherwise the GFUR partitioned hash join.
 

@@ -1210,7 +1210,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     return cuda_check(cudaGetLastError());
   }
 
-  // ---- SGB-DE (Sec. 4.1.3 with dictionary encoding): HGB stage 1 gives every
+  // ---- SGB-DE (SGB-TR of Sec. 4.1.3 after the dictionary encoding of Sec. 4.4): HGB stage 1 gives every
   // row a dense code and writes the dictionary (code -> key) to out_keys; the
   // codes are then sorted with the values on their ceil(log2 g) bits only and
   // reduced by the SGB kernels, whose segment i is code i. Reading g to size the

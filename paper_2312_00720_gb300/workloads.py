@@ -9,7 +9,7 @@ Workload shapes follow the paper's experimental setup:
 * join keys: R.key is a seeded permutation of 0..|R|-1 (Sec. 5.1.1); S.key is
   drawn from R's keys uniformly or with a Zipf law (Sec. 5.1.7, P(rank r) ~ r^-theta);
   a match ratio below one replaces exactly round((1-mr)|S|) foreign keys by
-  values outside R's key range (Sec. 5.1.5);
+  values outside R's key range (Sec. 5.1.6, "Match Ratio");
 * group keys: uniform over the domain {0..g-1} (Sec. 5.2.1) or Zipf over it
   (Sec. 5.2.7); 8-byte keys are a bijective 64-bit mix of the 4-byte domain id so
   that every key bit is live;
@@ -95,7 +95,7 @@ def join_workload(nr: int, ns: int, ncols_r: int, ncols_s: int, *, theta: float 
 def mn_join_workload(nr: int, ns: int, nk: int, ncols_r: int = 2, ncols_s: int = 2, *, key_dtype=np.int32,
                      col_dtype=np.int32, seed: int = 13):
     """Many-to-many join inputs: R.key and S.key drawn uniformly from a seeded set
-    of nk distinct keys (Sec. 5.1, many-to-many joins); payloads uniform in [0, 2^31)."""
+    of nk distinct keys (Sec. 5.1.9, many-to-many joins); payloads uniform in [0, 2^31)."""
     keys = _rng(seed, 0).permutation(max(nk, 1) * 4)[:max(nk, 1)].astype(key_dtype)
     rkey = keys[_rng(seed, 1).integers(0, max(nk, 1), size=nr)]
     skey = keys[_rng(seed, 2).integers(0, max(nk, 1), size=ns)]

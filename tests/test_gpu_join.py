@@ -136,7 +136,7 @@ def test_full_size_plain_join(gj, theta, mr, variant):
     assert np.array_equal(_fingerprint(t_side), _fingerprint(s_side))
 
 
-# ---- many-to-many (Sec. 5.1): R and S keys from a set of nk keys, every pair out
+# ---- many-to-many (Sec. 5.1.9): R and S keys from a set of nk keys, every pair out
 @pytest.mark.parametrize("nr,ns,nk,ncr,ncs", [
     (1, 1, 1, 1, 1), (100, 100, 1, 2, 2), (1000, 3000, 50, 2, 2), (20011, 30011, 5000, 2, 2),
     (65536, 65536, 1 << 13, 2, 2), (100000, 70000, 100000, 3, 1), (5000, 4000, 4000, 0, 0)])
