@@ -1,4 +1,4 @@
-// Grouped aggregation (paper Sec. 3.2, 4.1.3, 4.2, 4.3).
+// Grouped aggregation (paper Sec. 3.2, 4.1.3, 4.2, 4.3, 4.4).
 //
 // HGB (Sec. 4.2, Algorithm 1): stage 1 inserts every key with its tuple id into
 // a global hash table; the inserting tuple takes a dense group id from an atomic
