@@ -375,3 +375,22 @@ def test_zipf_foreign_keys_follow_the_primary_key_order():
         want = ns * p[r]
         assert abs(counts.get(int(w["rkey"][r]), 0) - want) < 5 * math.sqrt(want * (1 - p[r]))
     assert set(counts) <= set(int(x) for x in w["rkey"])
+
+
+def test_join_groupby_modulus_truncates_toward_zero():
+    # reading R9: the group key modulus is C's %, so negative values keep their sign
+    # (residues in (-m, m)); np.fmod is the same truncating remainder
+    rng = np.random.default_rng(17)
+    nr, ns = 60, 300
+    rkey = rng.permutation(nr)
+    skey = rng.integers(0, nr, ns)
+    rcols = [rng.integers(-1000, 1000, nr)]
+    scols = [rng.integers(-50, 50, ns)]
+    got = oracle.join_groupby(rkey, rcols, skey, scols, g_side=0, g_col=0, g_mod=7,
+                              aggs=["count", "sum", "min"], agg_side=[1, 1, 1], agg_col=[0, 0, 0])
+    t = brute_join(rkey, rcols, skey, scols)
+    gk = np.fmod(t[:, 1], 7)
+    assert gk.min() < 0                      # the case the reading is about occurs
+    want = brute_groupby(gk, [t[:, 2]], ["count", "sum", "min"], [0, 0, 0])
+    assert np.array_equal(oracle.canonical(got), oracle.canonical(want))
+    assert got[:, 0].min() > -7 and got[:, 0].max() < 7
