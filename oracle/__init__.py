@@ -12,10 +12,14 @@ Contents
     and M4 (Sec. 4.4), pinned to the printed "Estimated" series.
   * ``heuristics``: the join rule of Sec. 5.1.10 (join summary) / Sec. 7 and the group-by
     decision tree (Fig. groupby-dt).
-  * ``mlp``: float64 forward/backward of the variant-selector network.
+  * ``mlp``: float64 forward/backward of the variant-selector network and its
+    SGD and Adam updates.
 
 Parity status: every function here is pinned by tests under ``tests/`` (brute
-force, invariants, closed forms, the paper's printed numbers); none is unpinned.
+force, invariants, closed forms, the paper's printed numbers; the MLP by central
+finite differences, an affine special case, and Adam's closed forms: the first
+step from zero moments and every step of a constant gradient move each parameter
+by lr * g / (|g| + eps)); none is unpinned.
 """
 from __future__ import annotations
 

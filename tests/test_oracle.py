@@ -304,6 +304,52 @@ def test_mlp_linear_special_case():
     assert np.allclose(y, want, rtol=1e-12)
 
 
+def test_sgd_step_on_a_hand_computed_vector():
+    from oracle import mlp
+    theta = np.array([1.0, -2.0, 0.5, 0.0])
+    g = np.array([0.5, 4.0, -1.0, 3.0])
+    # theta - 0.25 * g, worked out by hand
+    assert np.array_equal(mlp.sgd_step(theta, g, 0.25), np.array([0.875, -3.0, 0.75, -0.75]))
+
+
+def test_adam_first_step_moves_by_lr_times_sign():
+    # from m = v = 0 the bias-corrected moments are g and g^2, so step 1 moves every
+    # parameter by lr * g / (|g| + eps) (Kingma & Ba 2015, Algorithm 1), whatever the betas
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    theta = rng.normal(0, 1, 50)
+    g = rng.normal(0, 1, 50) * 10.0 ** rng.integers(-3, 3, 50)
+    for b1, b2 in ((0.9, 0.999), (0.5, 0.9)):
+        new, m, v = mlp.adam_step(theta, g, np.zeros(50), np.zeros(50), 1, 0.01, b1, b2, 1e-8)
+        assert np.allclose(new, theta - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+        assert np.allclose(m, (1 - b1) * g) and np.allclose(v, (1 - b2) * g * g)
+
+
+def test_adam_constant_gradient_takes_the_same_step_every_time():
+    # with a constant gradient m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2: the bias
+    # corrections cancel exactly, so steps 1, 2 and 3 are equal
+    from oracle import mlp
+    g = np.array([0.3, -2.0, 1e-3, 5.0])
+    th, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    steps = []
+    for t in (1, 2, 3):
+        new, m, v = mlp.adam_step(th, g, m, v, t, 0.1)
+        steps.append(new - th)
+        th = new
+    want = -0.1 * g / (np.abs(g) + 1e-8)
+    for s in steps:
+        assert np.allclose(s, want, rtol=1e-12, atol=0)
+
+
+def test_adam_eps_is_added_after_the_square_root():
+    # a gradient far below eps: the step is lr * g / (|g| + eps), not lr * g / sqrt(g^2 + eps)
+    from oracle import mlp
+    g = np.array([1e-12, -3e-12])
+    new, _, _ = mlp.adam_step(np.zeros(2), g, np.zeros(2), np.zeros(2), 1, 1.0, eps=1e-8)
+    assert np.allclose(new, -g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert abs(new[0]) < 1.1e-4 and abs(new[0]) > 0.9e-4
+
+
 def test_many_to_many_generator_draws_from_nk_keys():
     a = wl.mn_join_workload(5000, 7000, 300, 2, 1, seed=4)
     b = wl.mn_join_workload(5000, 7000, 300, 2, 1, seed=4)
