@@ -160,16 +160,17 @@ gj_status gj_radix_partition(const gj_table* in, int32_t bit_lo, int32_t bit_hi,
  * the result is exactly gj_radix_partition's for one pass.
  * Limits: bit_hi - bit_lo <= 8 (a single pass) and in->n <= 2^21 rows, else
  * GJ_ERR_UNSUPPORTED; arguments as for gj_radix_partition otherwise.
- * Memory: the array is about 4 MB and is resident on every device that loads
- * the library until the process exits. The call makes no cudaMalloc, cudaFree
+ * Memory: the array is about 0.5 MB (per-tile digit offsets for 2^21 rows in
+ * tiles of 4096) and is resident on every device that loads the library until
+ * the process exits. The call makes no cudaMalloc, cudaFree
  * or allocator-hook call. Its first call on a device looks up the array's
  * device address with that device current; make that first call before any
  * stream capture. All calls share the one array, which keeps what the last call
  * left in it (each call clears the part it uses): calls whose work can overlap
  * on the GPU -- unordered streams or concurrent host threads -- race on it, so
  * the caller must order them. sync = 1 synchronises `stream` and returns the
- * errors its kernels recorded; with sync = 0 they are kept for the next sync = 1
- * call of this entry point. */
+ * errors its kernels recorded (an empty input included); with sync = 0 they are
+ * kept for the next sync = 1 call of this entry point. */
 gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
                                      gj_table* out, int64_t* d_offsets, int32_t sync, void* stream);
 

@@ -4,7 +4,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "gj_internal.cuh"
 
@@ -143,6 +145,24 @@ gj_status make_ctx(void* stream, Ctx* ctx) {
   ctx->num_sms = g_num_sms[dev];
   ctx->smem_optin = g_smem_optin[dev];
   ctx->device = dev;
+  return GJ_OK;
+}
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<const void*, int>, int> g_attr_bytes;  // (kernel, device) -> limit set
+}  // namespace
+
+gj_status ensure_smem_attr(const Ctx& ctx, const void* func, int bytes) {
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  auto key = std::make_pair(func, ctx.device);
+  auto it = g_attr_bytes.find(key);
+  if (it != g_attr_bytes.end() && it->second >= bytes) return GJ_OK;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return GJ_ERR_CUDA;
+  }
+  g_attr_bytes[key] = bytes;
   return GJ_OK;
 }
 

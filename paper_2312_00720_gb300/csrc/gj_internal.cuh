@@ -353,6 +353,11 @@ class Scratch {
 
 gj_status make_ctx(void* stream, Ctx* ctx);
 
+// Raises `func`'s dynamic shared-memory limit to `bytes` on the context's device,
+// once per (kernel, device) pair: the attribute belongs to the device context, so
+// a process that drives several GPUs sets it on each of them.
+gj_status ensure_smem_attr(const Ctx& ctx, const void* func, int bytes);
+
 // Kernel kinds for launch counting and the optional per-kernel event timing.
 enum KernelKind {
   KK_RADIX_HIST = 0,

@@ -1102,13 +1102,10 @@ gj_status sgb_reduce_run(const Ctx& ctx, Scratch& scr, const K* k2, int64_t n, c
   int64_t* bcarry = scr.get_as<int64_t>((size_t)nblk * rw);
   if (scr.failed()) return GJ_ERR_OOM;
   const size_t dyn = sizeof(int64_t) * ((size_t)2 * kSegWarps * nagg * 32 + (size_t)2 * kSegWarps * rw);
-  static bool attr[2] = {false, false};
-  if (!attr[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(
-        sgb_reduce_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)(sizeof(int64_t) * ((size_t)2 * kSegWarps * kMaxAggs * 32 + 2 * kSegWarps * (kMaxAggs + 2))));
-    attr[sizeof(K) == 8] = true;
-  }
+  gj_status st = ensure_smem_attr(
+      ctx, (const void*)sgb_reduce_kernel<K>,
+      (int)(sizeof(int64_t) * ((size_t)2 * kSegWarps * kMaxAggs * 32 + 2 * kSegWarps * (kMaxAggs + 2))));
+  if (st != GJ_OK) return st;
   // the distinct 4-byte value columns (up to kSegCache) are kept in registers
   SegCols sc{};
   sc.tid = A.tid;
@@ -1197,11 +1194,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
         }
       }
     const int budget = ctx.smem_optin - 1024;  // all of an SM's opt-in shared memory for one block
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(hgb_agg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, budget);
-      attr = true;
-    }
+    if ((st = ensure_smem_attr(ctx, (const void*)hgb_agg_kernel, budget)) != GJ_OK) return st;
     {
       LaunchScope ls(ctx, KK_HGB_AGG);
       hgb_agg_kernel<<<ctx.num_sms, 1024, budget, s>>>(gidloc, gid_of_row, n, A, make_col_cache(A), L, d_ngroups,
@@ -1331,11 +1324,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, k2, n, 0, bits, kHashed, poff)) != GJ_OK)
     return st;
   const size_t dyn = pgb_smem_bytes<K>();
-  static bool attr[2] = {false, false};
-  if (!attr[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(pgb_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    attr[sizeof(K) == 8] = true;
-  }
+  if ((st = ensure_smem_attr(ctx, (const void*)pgb_kernel<K>, (int)dyn)) != GJ_OK) return st;
   const ColCache cc = make_col_cache(A);
   // group counts per partition, their exclusive scan (and g), then the aggregation
   {

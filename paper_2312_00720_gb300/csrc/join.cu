@@ -1369,11 +1369,7 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if ((st = cuda_check(cudaMemsetAsync(ustat, 0, sizeof(uint64_t) * nunits, s))) != GJ_OK) return st;
   if ((st = cuda_check(cudaMemsetAsync(ucounter, 0, sizeof(int), s))) != GJ_OK) return st;
   const size_t dyn = phj_unit_smem_bytes<K>();
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(phj_unit_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    attr_set[sizeof(K) == 8] = true;
-  }
+  if ((st = ensure_smem_attr(ctx, (const void*)phj_unit_kernel<K>, (int)dyn)) != GJ_OK) return st;
   LaunchScope ls(ctx, KK_PHJ_PROBE);
   phj_unit_kernel<K><<<(unsigned)nunits, kThreads, dyn, s>>>(rk, roff, bits, sk, ns, io, ustat, ucounter, nunits,
                                                               ctx.d_status);
@@ -1513,23 +1509,16 @@ gj_status join_groupby_typed(const Ctx& ctx, const gj_table* R, const gj_table* 
 
   const size_t agg_dyn = G.smem ? smem_agg : 0;
   if (variant == GJ_JOIN_NPHJ) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(nphj_probe_agg_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      attr = true;
-    }
+    if ((st = ensure_smem_attr(ctx, (const void*)nphj_probe_agg_kernel<K>, 96 * 1024)) != GJ_OK) return st;
     LaunchScope ls(ctx, KK_FUSED_PROBE);
     int blocks = (int)std::min<int64_t>((ns + kThreads - 1) / kThreads, (int64_t)ctx.num_sms * 4);
     nphj_probe_agg_kernel<K><<<blocks, kThreads, agg_dyn, s>>>(rk, ht, ht_slots - 1, sk, ns, G, ctx.d_status);
   } else {
     const int64_t ntiles = (ns + kTileS - 1) / kTileS;
     const size_t dyn = phj_smem_bytes<K>() + agg_dyn;
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(phj_probe_agg_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(phj_smem_bytes<K>() + 96 * 1024));
-      attr = true;
-    }
+    if ((st = ensure_smem_attr(ctx, (const void*)phj_probe_agg_kernel<K>, (int)(phj_smem_bytes<K>() + 96 * 1024))) !=
+        GJ_OK)
+      return st;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phj_probe_agg_kernel<K>, kThreads, dyn);
     int blocks = (int)std::min<int64_t>(ntiles, (int64_t)ctx.num_sms * std::max(per_sm, 1));

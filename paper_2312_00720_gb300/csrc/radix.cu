@@ -37,6 +37,15 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxChunks = 8;  // 32-row chunks per warp: tiles of up to 4096 rows
 constexpr int kSmemBudget = 48 * 1024;  // staged key + per-row arrays; three blocks per SM
 
+// 32-row chunks per warp for a key of key_size bytes: the staged key and 4 bytes of
+// permutation per row within the budget. Tiles hold kThreads * chunks rows (4096
+// for 4- and 8-byte keys).
+constexpr int scatter_chunks(int key_size) {
+  return kSmemBudget / (kThreads * (key_size + 4)) < 1 ? 1
+         : (kSmemBudget / (kThreads * (key_size + 4)) > kMaxChunks ? kMaxChunks
+                                                                    : kSmemBudget / (kThreads * (key_size + 4)));
+}
+
 
 // Exclusive scan of one value per thread over the block.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp) {
@@ -414,9 +423,7 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   uint32_t gen_mask = 0;
   for (int c = 0; c < cols_in.n; ++c)
     if (cols_in.src[c] == nullptr) gen_mask |= 1u << c;
-  // tile: 512 rows per chunk step; staged key + 4 bytes/row of permutation within the budget
-  int chunks = kSmemBudget / (kThreads * ((int)sizeof(K) + 4));
-  chunks = std::max(1, std::min(kMaxChunks, chunks));
+  const int chunks = scatter_chunks((int)sizeof(K));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
 
@@ -442,11 +449,7 @@ gj_status radix_partition_typed(const Ctx& ctx, Scratch& scr, const K* kin, K* k
   cudaStream_t s = ctx.stream;
   gj_status st;
   if ((st = cuda_check(cudaMemsetAsync(total, 0, sizeof(uint32_t) * plan.passes * kRadixMax, s))) != GJ_OK) return st;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(K) == 8]) {
-    cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget + 16 * 1024);
-    attr_set[sizeof(K) == 8] = true;
-  }
+  if ((st = ensure_smem_attr(ctx, (const void*)radix_scatter_kernel<K>, kSmemBudget + 16 * 1024)) != GJ_OK) return st;
   for (int q = 0; q < plan.passes; ++q) {
     const bool to_out = ((plan.passes - 1 - q) % 2) == 0;
     ScatterArgs a{};
@@ -536,10 +539,14 @@ gj_status radix_partition_run(const Ctx& ctx, Scratch& scr, int key_type, const 
 // For callers that cannot allocate device memory: a single-pass partition whose
 // scratch (digit totals, per-tile digit offsets) is this file-scope
 // array instead of stream-ordered allocations. It holds kNoAllocWords 32-bit
-// words (about 4 MB) on every device that loads the library, until exit.
+// words (about 0.5 MB) on every device that loads the library, until exit.
 namespace {
 constexpr int64_t kNoAllocMaxRows = int64_t(1) << 21;
-constexpr int kNoAllocMaxTiles = (int)(kNoAllocMaxRows / kThreads);  // tiles hold >= 512 rows
+// tiles of the smaller of the two key widths' tile sizes bound the tile count
+constexpr int kNoAllocTileRows =
+    kThreads * (scatter_chunks(4) < scatter_chunks(8) ? scatter_chunks(4) : scatter_chunks(8));
+constexpr int kNoAllocMaxTiles = (int)((kNoAllocMaxRows + kNoAllocTileRows - 1) / kNoAllocTileRows);
+static_assert(kNoAllocMaxTiles % 4 == 0, "the offset rows are padded to a multiple of 4 tiles");
 constexpr size_t kNoAllocHead = 320;                                  // digit totals (256), padded
 constexpr size_t kNoAllocWords = kNoAllocHead + (size_t)kNoAllocMaxTiles * kRadixMax;
 __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
@@ -561,9 +568,10 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
     cols.dst[c] = out->cols[c];
     cols.size[c] = dtype_size(in->col_type[c]);
   }
-  int chunks = std::max(1, std::min(kMaxChunks, kSmemBudget / (kThreads * ((int)sizeof(K) + 4))));
+  const int chunks = scatter_chunks((int)sizeof(K));
   const int tile_rows = kThreads * chunks;
   const int64_t tiles = (n + tile_rows - 1) / tile_rows;
+  if (tiles > kNoAllocMaxTiles) return GJ_ERR_UNSUPPORTED;  // not reached: n <= kNoAllocMaxRows
   ScatterArgs a{};
   a.kin = in->key;
   a.kout = out->key;
@@ -597,9 +605,7 @@ gj_status noalloc_partition(const Ctx& ctx, uint32_t* scratch, const gj_table* i
     LaunchScope ls(ctx, KK_RADIX_HIST);
     tile_offsets_kernel<<<1u << width, 1024, 0, s>>>(scratch + kNoAllocHead, scratch, a.ld);
   }
-  if ((st = cuda_check(cudaFuncSetAttribute(radix_scatter_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSmemBudget + 16 * 1024))) != GJ_OK)
-    return st;
+  if ((st = ensure_smem_attr(ctx, (const void*)radix_scatter_kernel<K>, kSmemBudget + 16 * 1024)) != GJ_OK) return st;
   {
     LaunchScope ls(ctx, KK_RADIX_SCATTER);
     radix_scatter_kernel<K><<<(unsigned)tiles, kThreads, (size_t)off, s>>>(a);
@@ -664,16 +670,17 @@ extern "C" gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_
   ctx.device = dev;
   cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&ctx.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (in->n == 0) {
-    if (d_offsets) return partition_bounds_run(ctx, in->key_type, out->key, 0, bit_lo, bit_hi - bit_lo, key_transform,
-                                               d_offsets);
-    return GJ_OK;
-  }
-  gj_status st = in->key_type == GJ_I64
-                     ? noalloc_partition<int64_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform,
-                                                  d_offsets)
-                     : noalloc_partition<int32_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform,
-                                                  d_offsets);
+  gj_status st;
+  if (in->n == 0)  // nothing to move; the bounds are all zero
+    st = d_offsets ? partition_bounds_run(ctx, in->key_type, out->key, 0, bit_lo, bit_hi - bit_lo, key_transform,
+                                          d_offsets)
+                   : GJ_OK;
+  else
+    st = in->key_type == GJ_I64
+             ? noalloc_partition<int64_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform, d_offsets)
+             : noalloc_partition<int32_t>(ctx, g_noalloc_ptr[dev], in, out, bit_lo, bit_hi, key_transform, d_offsets);
+  // every call, empty or not, ends the same way: with sync = 1 it returns (and
+  // clears) what its kernels and earlier sync = 0 calls recorded
   if (st != GJ_OK || !sync) return st;
   int h = 0;
   if (cudaStreamSynchronize(ctx.stream) != cudaSuccess) return GJ_ERR_CUDA;
