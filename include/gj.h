@@ -316,7 +316,9 @@ gj_status gj_mlp_select(const float* theta, const float* x, int32_t n, int32_t* 
  *   4 S payload columns  5 Zipf factor  6 match ratio  7 log2(groups+1)
  *   8 aggregates  9 log2((|R|+1)/(|S|+1))  10 payload bytes per S row
  *   11 log2(groups+1) / log2(|S|+2)
- * with options' hints standing in for unknown skew, match ratio and groups. */
+ * with options' hints standing in for unknown skew, match ratio and groups.
+ * Features a call knows nothing about take the training mean (0 after
+ * normalisation): 7, 8 and 11 for gj_join, 0, 3, 6 and 9 for gj_groupby. */
 gj_status gj_selector_set(const float* host_theta, const float* mean, const float* stdev);
 /* The variants AUTO would run under the paper's rules (GJ_SELECT_HEURISTIC):
  * for the join, Sec. 7 (GFTR partitioned join if the match ratio is >= 25 %,
@@ -327,9 +329,38 @@ gj_status gj_selector_set(const float* host_theta, const float* mean, const floa
  * the column pointers of R and S may be NULL. `S` is the group-by input. */
 gj_status gj_heuristic_choose(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt,
                               int32_t* join_variant, int32_t* gb_variant);
+/* The variants an AUTO request would run (host only, no device work): for the
+ * join of R and S as gj_join runs it (fused = 0) or as gj_join_groupby runs it
+ * with nagg aggregates (fused = 1; it implements PHJ-TR, PHJ-UR and NPHJ); for
+ * the group-by of S with nagg aggregates ops[] (ops may be NULL: 8-byte slots) as
+ * gj_groupby runs it. Explicit variants in *opt are returned unchanged; AUTO
+ * follows opt->selector as the operators do. Either output pointer may be NULL. */
+gj_status gj_auto_variants(const gj_table* R, const gj_table* S, int32_t nagg, const int32_t* ops,
+                           const gj_options* opt, int32_t fused, int32_t* join_variant, int32_t* gb_variant);
 /* Writes the 12 raw features of a query into out[12] (host). Either table may be
  * NULL when only one operator is chosen. */
 gj_status gj_query_features(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt, float* out);
+
+/* ---- Bounded waits (no counterpart in the paper) ---------------------------
+ * Kernels that wait on other blocks (look-backs over tiles, bulk-copy
+ * mbarriers, the batched mode's task dependencies) give up once a wait has
+ * lasted longer than the current device's wait limit, record GJ_ERR_TIMEOUT and
+ * finish, so no launch of this library can hang its GPU.
+ *
+ * gj_set_wait_limit sets the limit of the waits on other blocks, in
+ * nanoseconds of the GPU's global timer, for launches made on the current device
+ * after it returns; 0 restores the default of 2 s. A short limit makes
+ * legitimate waits fail too (the results are then wrong, but every write stays
+ * inside the caller's buffers): it is meant for testing the failure path. A
+ * block's wait for its own bulk copies keeps the 2 s limit whatever is set.
+ *
+ * gj_check_bounded_wait runs one of those waits on a flag that nothing ever
+ * sets -- kind 0: the warp-wide look-back over a predecessor tile that never
+ * publishes; 1: an mbarrier that nothing arrives at; 2: a task counter that
+ * never reaches its target -- synchronises `stream` and returns (and clears) the
+ * device status, GJ_ERR_TIMEOUT when the wait gave up as it should. */
+gj_status gj_set_wait_limit(uint64_t ns);
+gj_status gj_check_bounded_wait(int32_t kind, void* stream);
 
 /* ---- Measurement support (no counterpart in the paper) -------------------
  * gj_profile_enable(1) makes every kernel launch of the library record a CUDA

@@ -122,9 +122,10 @@ gj_status make_ctx(void* stream, Ctx* ctx) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GJ_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_status_word[dev]) {
+    // status word at [0], the wait limit (ns, 0 = default) at bytes 8..15
     int* p = nullptr;
-    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return GJ_ERR_OOM;
-    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return GJ_ERR_CUDA;
+    if (cudaMalloc(&p, sizeof(int) * kStatusInts) != cudaSuccess) return GJ_ERR_OOM;
+    if (cudaMemset(p, 0, sizeof(int) * kStatusInts) != cudaSuccess) return GJ_ERR_CUDA;
     g_status_word[dev] = p;
     cudaDeviceGetAttribute(&g_num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&g_smem_optin[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -164,6 +165,25 @@ gj_status ensure_smem_attr(const Ctx& ctx, const void* func, int bytes) {
   }
   g_attr_bytes[key] = bytes;
   return GJ_OK;
+}
+
+// Waits that nothing ever releases, one kind per launch, for gj_check_bounded_wait:
+// 0 the warp-wide look-back over a predecessor that never publishes, 1 an mbarrier
+// that nothing arrives at, 2 a task counter that never reaches its target.
+__global__ void wait_check_kernel(int kind, uint64_t* words, int* status) {
+  __shared__ __align__(8) uint64_t s_bar;
+  if (kind == 0) {
+    if (threadIdx.x < 32) lookback_scan_warp(words, 1, 1, status);  // tile 0 never publishes
+  } else if (kind == 1) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&s_bar, 0, status);  // no arrival, no copy in flight
+  } else {
+    block_wait((const unsigned long long*)words + 1, 1ull, status);  // word 1 stays 0
+  }
 }
 
 gj_status read_and_clear_status(const Ctx& ctx) {
@@ -366,6 +386,48 @@ gj_status gj_heuristic_choose(const gj_table* R, const gj_table* S, int32_t nagg
     *gb_variant = choose_groupby_variant(S, nagg, nullptr, opt, std::min(smem, 200 * 1024));
   }
   return GJ_OK;
+}
+
+gj_status gj_auto_variants(const gj_table* R, const gj_table* S, int32_t nagg, const int32_t* ops,
+                           const gj_options* opt, int32_t fused, int32_t* join_variant, int32_t* gb_variant) {
+  gj_options defaults;
+  gj_options_default(&defaults);
+  if (!opt) opt = &defaults;
+  if (join_variant) {
+    if (!R || !S) return GJ_ERR_INVALID_ARG;
+    *join_variant = resolve_join_variant(R, S, fused ? nagg : 0, opt, fused != 0);
+  }
+  if (gb_variant) {
+    if (!S || nagg < 1) return GJ_ERR_INVALID_ARG;
+    int dev = 0, smem = 200 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaGetLastError();
+    *gb_variant = resolve_groupby_variant(S, nagg, ops, opt, std::min(smem, 200 * 1024) - 1024);
+  }
+  return GJ_OK;
+}
+
+gj_status gj_set_wait_limit(uint64_t ns) {
+  Ctx ctx;
+  gj_status st = make_ctx(nullptr, &ctx);
+  if (st != GJ_OK) return st;
+  return cuda_check(cudaMemcpy(ctx.d_status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice));
+}
+
+gj_status gj_check_bounded_wait(int32_t kind, void* stream) {
+  if (kind < 0 || kind > 2) return GJ_ERR_INVALID_ARG;
+  Ctx ctx;
+  gj_status st = make_ctx(stream, &ctx);
+  if (st != GJ_OK) return st;
+  {
+    Scratch scr(ctx.stream);
+    uint64_t* words = scr.get_as<uint64_t>(2);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(words, 0, 2 * sizeof(uint64_t), ctx.stream))) != GJ_OK) return st;
+    wait_check_kernel<<<1, 64, 0, ctx.stream>>>(kind, words, ctx.d_status);
+    if ((st = cuda_check(cudaGetLastError())) != GJ_OK) return st;
+  }
+  return read_and_clear_status(ctx);
 }
 
 void gj_profile_enable(int32_t on) { g_timing.store(on ? 1 : 0); }

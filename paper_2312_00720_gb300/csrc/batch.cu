@@ -90,29 +90,6 @@ __device__ __forceinline__ int64_t bref_value(const BRef& f, int64_t m, int64_t 
   return f.mod > 0 ? v % f.mod : v;
 }
 
-// Thread 0 waits until *p >= target (bounded), then the block proceeds.
-__device__ __forceinline__ void block_wait(const unsigned long long* p, unsigned long long target, int* err) {
-  if (threadIdx.x == 0) {
-    uint32_t spins = 0;
-    while (ld_volatile((const uint64_t*)p) < target) {
-      if (++spins > kSpinLimit) {
-        set_status(err, GJ_ERR_TIMEOUT);
-        break;
-      }
-      __nanosleep(100);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
-
-// Makes this block's writes visible, then counts the task as done.
-__device__ __forceinline__ void block_done(unsigned long long* p) {
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(p, 1ull);
-}
-
 __global__ void __launch_bounds__(kBThreads) batch_kernel(const BInst* __restrict__ insts,
                                                           const BTask* __restrict__ tasks, int ntasks,
                                                           unsigned long long* ctl, int* err) {

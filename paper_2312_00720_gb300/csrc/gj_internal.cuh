@@ -14,9 +14,14 @@ constexpr int kMaxCols = GJ_MAX_COLS;
 constexpr int kMaxAggs = GJ_MAX_AGGS;
 constexpr int64_t kMaxRows = (int64_t(1) << 30) - 1;
 
-// Bounded spin for cross-block waits: after this many polls the waiter records
+// Bounded waits. Every kernel receives its device's status buffer: the status
+// word at int [0] and, at bytes 8..15, the wait limit in nanoseconds (0 = the
+// default of kDefaultWaitNs). A waiter reads %globaltimer every kWaitPollsPerCheck
+// polls and, once the limit has passed since its first poll, records
 // GJ_ERR_TIMEOUT and proceeds with what it has, so a kernel always terminates.
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;  // 2 s
+constexpr uint32_t kWaitPollsPerCheck = 64;
+constexpr int kStatusInts = 4;  // ints in a status buffer
 
 // ------------------------------------------------------------------ hashing
 // MurmurHash3 fmix32 / fmix64 finalisers (Appleby, public domain): bijective
@@ -79,6 +84,37 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 // ------------------------------------------------------------------ status
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The clock of one bounded wait. expired() is called once per poll; calls made in
+// lockstep by the lanes of a warp see the same poll count, so a warp-wide vote on
+// it (__any_sync) keeps the warp's decision uniform.
+struct WaitGuard {
+  uint64_t start;
+  uint64_t limit;
+  uint32_t polls;
+  // a wait on other blocks: the device's current limit
+  __device__ __forceinline__ explicit WaitGuard(const int* status) : start(0), polls(0) {
+    const uint64_t l = *(const volatile uint64_t*)(status + 2);
+    limit = l ? l : kDefaultWaitNs;
+  }
+  // a wait with a fixed limit
+  __device__ __forceinline__ explicit WaitGuard(uint64_t limit_ns) : start(0), limit(limit_ns), polls(0) {}
+  __device__ __forceinline__ bool expired() {
+    if ((polls++ % kWaitPollsPerCheck) != 0) return false;
+    const uint64_t now = global_ns();
+    if (polls == 1) {
+      start = now;
+      return false;
+    }
+    return now - start >= limit;
+  }
+};
+
 // ------------------------------------------------------------------ look-back
 // Chained scan across tiles taken in order (decoupled look-back, Merrill &
 // Garland 2016). A tile's 64-bit word holds a 2-bit flag in the top bits and a
@@ -91,34 +127,6 @@ __device__ __forceinline__ uint64_t ld_volatile(const uint64_t* p) { return *(vo
 __device__ __forceinline__ void st_volatile(uint64_t* p, uint64_t v) { *(volatile uint64_t*)p = v; }
 __device__ __forceinline__ uint32_t ld_volatile32(const uint32_t* p) { return *(volatile const uint32_t*)p; }
 __device__ __forceinline__ void st_volatile32(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
-
-// Called by one thread of tile `tile`: publishes `agg`, returns the exclusive
-// prefix over tiles 0..tile-1 and publishes the inclusive value.
-__device__ __forceinline__ uint64_t lookback_scan(uint64_t* st, int64_t tile, uint64_t agg, int* status) {
-  if (tile == 0) {
-    st_volatile(&st[0], kFlagInc | agg);
-    return 0;
-  }
-  st_volatile(&st[tile], kFlagAgg | agg);
-  uint64_t excl = 0;
-  int64_t t = tile - 1;
-  uint32_t spins = 0;
-  while (t >= 0) {
-    uint64_t w = ld_volatile(&st[t]);
-    if ((w & ~kValMask) == 0) {
-      if (++spins > kSpinLimit) {
-        set_status(status, GJ_ERR_TIMEOUT);
-        break;
-      }
-      continue;
-    }
-    excl += w & kValMask;
-    if ((w & ~kValMask) == kFlagInc) break;
-    --t;
-  }
-  st_volatile(&st[tile], kFlagInc | (excl + agg));
-  return excl;
-}
 
 // Warp-wide look-back: called by all 32 lanes of one warp of tile `tile`. Lanes
 // read 32 predecessors per round trip (lane l reads tile base - l), so a chain
@@ -134,14 +142,14 @@ __device__ __forceinline__ uint64_t lookback_scan_warp(uint64_t* st, int64_t til
   if (lane == 0) st_volatile(&st[tile], kFlagAgg | agg);
   uint64_t excl = 0;
   int64_t base = tile - 1;
-  uint32_t spins = 0;
+  WaitGuard guard(status);
   bool timed_out = false;
   while (base >= 0) {
     const int64_t idx = base - lane;
     uint64_t w = idx >= 0 ? ld_volatile(&st[idx]) : kFlagInc;
     // every predecessor was taken by a running block: wait until all 32 have a flag
     while (__any_sync(0xffffffffu, (w & ~kValMask) == 0)) {
-      if (++spins > kSpinLimit) {
+      if (__any_sync(0xffffffffu, guard.expired())) {  // every lane polls in lockstep: a uniform decision
         timed_out = true;
         break;
       }
@@ -163,6 +171,30 @@ __device__ __forceinline__ uint64_t lookback_scan_warp(uint64_t* st, int64_t til
   if (lane == 0) st_volatile(&st[tile], kFlagInc | (excl + agg));
   __syncwarp();
   return excl;
+}
+
+// Thread 0 waits until the counter *p reaches target (bounded), then the whole
+// block proceeds: a task's wait for the tasks it depends on.
+__device__ __forceinline__ void block_wait(const unsigned long long* p, unsigned long long target, int* err) {
+  if (threadIdx.x == 0) {
+    WaitGuard guard(err);
+    while (ld_volatile((const uint64_t*)p) < target) {
+      if (guard.expired()) {
+        set_status(err, GJ_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Makes this block's writes visible, then counts its task as done.
+__device__ __forceinline__ void block_done(unsigned long long* p) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(p, 1ull);
 }
 
 // ------------------------------------------------------------------ bulk copies
@@ -198,12 +230,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: after kSpinLimit polls the error is recorded and the caller
-// proceeds, so the kernel always ends.
+// Bounded wait for this block's own bulk copies: after kDefaultWaitNs the error is
+// recorded and the caller proceeds, so the kernel always ends. The limit is fixed
+// (gj_set_wait_limit does not shorten it): a copy still in flight must land
+// before its block may use or leave the shared memory it writes, and no working
+// copy takes anywhere near that long.
 __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t phase, int* err) {
-  uint32_t spins = 0;
+  WaitGuard guard(kDefaultWaitNs);
   while (!mbar_try_wait(bar, phase)) {
-    if (++spins > kSpinLimit) {
+    if (guard.expired()) {
       set_status(err, GJ_ERR_TIMEOUT);
       return;
     }
@@ -426,8 +461,17 @@ int heuristic_join_variant(const gj_table* R, const gj_options* opt);
 int choose_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt, int smem_budget);
 
 // Learned selector: raw query features, and the network's choice (0 = no network).
+// `fused` restricts a join choice to the variants the join -> group-by call runs
+// (PHJ-TR, PHJ-UR, NPHJ).
 void query_features(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, float* f);
-int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join);
+int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join, bool fused);
+
+// The variants an AUTO request runs: the trained network's choice when
+// options.selector is GJ_SELECT_MLP and a network is installed, else the paper's
+// rules; an explicit variant is returned unchanged.
+int resolve_join_variant(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool fused);
+int resolve_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt,
+                            int smem_budget);
 
 // Total partition bits for a build side of nr rows so that a partition holds
 // about `target` rows; at most 16 bits (two passes of 8).

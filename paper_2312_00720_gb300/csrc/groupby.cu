@@ -1356,12 +1356,18 @@ int choose_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, con
   return GJ_GB_PGB;
 }
 
+int resolve_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt,
+                            int smem_budget) {
+  int variant = opt->groupby_variant;
+  if (variant == GJ_GB_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(nullptr, in, nagg, opt, false, false);
+  if (variant == GJ_GB_AUTO) variant = choose_groupby_variant(in, nagg, ops, opt, smem_budget);
+  return variant;
+}
+
 gj_status groupby_run(const Ctx& ctx, const gj_table* in, int nagg, const int32_t* ops, const int32_t* op_col,
                       const gj_options* opt, void* out_keys, int64_t* const* out_aggs, int64_t cap,
                       int64_t* d_ngroups) {
-  int variant = opt->groupby_variant;
-  if (variant == GJ_GB_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(nullptr, in, nagg, opt, false);
-  if (variant == GJ_GB_AUTO) variant = choose_groupby_variant(in, nagg, ops, opt, ctx.smem_optin - 1024);
+  const int variant = resolve_groupby_variant(in, nagg, ops, opt, ctx.smem_optin - 1024);
   if (in->key_type == GJ_I64)
     return groupby_typed<int64_t>(ctx, in, nagg, ops, op_col, opt, variant, out_keys, out_aggs, cap, d_ngroups);
   return groupby_typed<int32_t>(ctx, in, nagg, ops, op_col, opt, variant, out_keys, out_aggs, cap, d_ngroups);

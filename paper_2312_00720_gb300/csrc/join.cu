@@ -1544,10 +1544,7 @@ gj_status join_groupby_typed(const Ctx& ctx, const gj_table* R, const gj_table* 
 gj_status join_groupby_run(const Ctx& ctx, const gj_table* R, const gj_table* S, gj_colref gk, int nagg,
                            const int32_t* ops, const gj_colref* agg_cols, const gj_options* opt, int64_t* out_keys,
                            int64_t* const* out_aggs, int64_t cap, int64_t* d_ngroups) {
-  int variant = opt->join_variant;
-  // a global table on a build side of a few million rows stays in L2; larger
-  // build sides are partitioned
-  if (variant == GJ_JOIN_AUTO) variant = R->n <= (int64_t(1) << 22) ? GJ_JOIN_NPHJ : GJ_JOIN_PHJ_TR;
+  const int variant = resolve_join_variant(R, S, nagg, opt, true);
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 512);
   if (R->key_type == GJ_I64)
     return join_groupby_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, gk, nagg, ops, agg_cols, opt,
@@ -1572,11 +1569,16 @@ int heuristic_join_variant(const gj_table* R, const gj_options* opt) {
   return (mr >= 0.25f || z >= 0.5f || R->key_type == GJ_I64) ? GJ_JOIN_PHJ_TR : GJ_JOIN_PHJ_UR;
 }
 
+int resolve_join_variant(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool fused) {
+  int variant = opt->join_variant;
+  if (variant == GJ_JOIN_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(R, S, nagg, opt, true, fused);
+  if (variant == GJ_JOIN_AUTO) variant = heuristic_join_variant(R, opt);
+  return variant;
+}
+
 gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const gj_options* opt, gj_table* T,
                    int64_t cap, int64_t* d_count) {
-  int variant = opt->join_variant;
-  if (variant == GJ_JOIN_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(R, S, 0, opt, true);
-  if (variant == GJ_JOIN_AUTO) variant = heuristic_join_variant(R, opt);
+  const int variant = resolve_join_variant(R, S, 0, opt, false);
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 512);
   if (R->key_type == GJ_I64)
     return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);

@@ -216,12 +216,16 @@ void query_features(const gj_table* R, const gj_table* S, int nagg, const gj_opt
 }
 
 // Variant choice of the trained network, or 0 when no network is set.
-int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join) {
+int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join, bool fused) {
   std::lock_guard<std::mutex> lock(g_sel_mu);
   if (!g_sel_on) return 0;
   float f[kIn], y[kOut];
   query_features(R, S, nagg, opt, f);
   for (int i = 0; i < kIn; ++i) f[i] = (f[i] - g_sel_mean[i]) / g_sel_std[i];
+  // features the call knows nothing about take the training mean (0 once
+  // normalised): the group-by's for a join alone, the join's for a group-by alone
+  if (join && !fused) f[7] = f[8] = f[11] = 0.f;
+  if (!join) f[0] = f[3] = f[6] = f[9] = 0.f;
   host_forward(g_sel_theta.data(), f, y);
   if (join) {
     int b = 0;

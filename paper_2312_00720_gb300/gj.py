@@ -86,8 +86,48 @@ def load():
     lib.gj_kernel_name.restype = ctypes.c_char_p
     lib.gj_kernel_launches.argtypes = []
     lib.gj_kernel_launches.restype = i64
+    lib.gj_set_wait_limit.argtypes = [ctypes.c_uint64]
+    lib.gj_set_wait_limit.restype = i32
+    lib.gj_check_bounded_wait.argtypes = [i32, p]
+    lib.gj_check_bounded_wait.restype = i32
     _lib = lib
     return lib
+
+
+# C types of the scratch allocator hooks (gj_set_allocator)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = None  # keeps the installed ctypes callbacks alive
+
+
+def set_allocator(alloc=None, free=None):
+    """Installs Python scratch-allocator hooks (gj_set_allocator): alloc(bytes,
+    stream) returns a device address or 0 (the call then fails with GJ_ERR_OOM),
+    free(ptr, stream) releases one. No arguments restores the library's own
+    stream-ordered allocations."""
+    global _hooks
+    lib = load()
+    if alloc is None:
+        _raise(lib.gj_set_allocator(None, None, None), "gj_set_allocator")
+        _hooks = None
+        return
+    a = ALLOC_FN(lambda nbytes, stream, ctx: alloc(int(nbytes), stream) or None)
+    f = FREE_FN(lambda ptr, stream, ctx: free(int(ptr), stream))
+    _raise(lib.gj_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None),
+           "gj_set_allocator")
+    _hooks = (a, f)
+
+
+def set_wait_limit(ns: int):
+    """Wait limit of the library's bounded device-side waits on the current
+    device, in nanoseconds (0 = the default of 2 s)."""
+    _raise(load().gj_set_wait_limit(int(ns)), "gj_set_wait_limit")
+
+
+def check_bounded_wait(kind: int) -> int:
+    """Runs bounded wait `kind` (0 look-back, 1 mbarrier, 2 task counter) on a flag
+    nothing sets; returns the status the kernel recorded (6 = GJ_ERR_TIMEOUT)."""
+    return int(load().gj_check_bounded_wait(kind, _stream()))
 
 
 BATCH_MAX_AGGS = 8
@@ -204,8 +244,9 @@ def _load_mlp(lib):
     lib.gj_selector_set.argtypes = [p, p, p]
     lib.gj_query_features.argtypes = [P(Table), P(Table), i32, P(Options), p]
     lib.gj_heuristic_choose.argtypes = [P(Table), P(Table), i32, P(Options), P(i32), P(i32)]
+    lib.gj_auto_variants.argtypes = [P(Table), P(Table), i32, p, P(Options), i32, P(i32), P(i32)]
     for f in ("gj_mlp_forward", "gj_mlp_loss_grad", "gj_mlp_adam_step", "gj_mlp_sgd_step", "gj_mlp_select",
-              "gj_selector_set", "gj_query_features", "gj_heuristic_choose"):
+              "gj_selector_set", "gj_query_features", "gj_heuristic_choose", "gj_auto_variants"):
         getattr(lib, f).restype = i32
     lib._mlp_ready = True
 
@@ -308,6 +349,23 @@ def heuristic_choose(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups
     jv, gv = ctypes.c_int32(), ctypes.c_int32()
     _raise(lib.gj_heuristic_choose(ctypes.byref(R), ctypes.byref(S), nagg, ctypes.byref(o), ctypes.byref(jv),
                                    ctypes.byref(gv)), "gj_heuristic_choose")
+    return jv.value, gv.value
+
+
+def auto_variants(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups, *, selector: int = 0,
+                  fused: bool = False, join: str = "auto", groupby: str = "auto"):
+    """(join variant, group-by variant) that AUTO requests run (gj_auto_variants):
+    the join of gj_join (fused = False) or gj_join_groupby (fused = True), the
+    group-by of gj_groupby over the S-shaped input; host only."""
+    lib = load()
+    _load_mlp(lib)
+    R = _shape_table(nr, key_bytes, ncols_r)
+    S = _shape_table(ns, key_bytes, ncols_s)
+    o = options(join=join, groupby=groupby, zipf_hint=zipf, match_ratio_hint=mr, groups_hint=int(groups),
+                selector=selector)
+    jv, gv = ctypes.c_int32(), ctypes.c_int32()
+    _raise(lib.gj_auto_variants(ctypes.byref(R), ctypes.byref(S), nagg, None, ctypes.byref(o), 1 if fused else 0,
+                                ctypes.byref(jv), ctypes.byref(gv)), "gj_auto_variants")
     return jv.value, gv.value
 
 

@@ -65,3 +65,41 @@ def test_initial_parameters_follow_the_network_layout():
         assert np.all(p[b] == 0.0)
     for w, fan_in in (("w1", 12), ("w2", 64), ("w3", 64)):
         assert abs(p[w].std() - np.sqrt(2.0 / fan_in)) < 0.25 * np.sqrt(2.0 / fan_in)
+
+
+def _network_preferring(join_idx: int, gb_idx: int):
+    # all weights zero, output biases alone: y = b3, so the argmins are fixed
+    from oracle import mlp
+    th = np.zeros(mlp.N_PARAMS)
+    p = mlp.unpack(th)
+    b3 = np.ones(mlp.D_OUT)
+    b3[join_idx] = -1.0
+    b3[3 + gb_idx] = -1.0
+    return mlp.pack({**p, "b3": b3}).astype(np.float32)
+
+
+@pytest.mark.parametrize("join_idx", [0, 1, 2])
+def test_fused_call_resolves_auto_like_the_join_under_the_network(join_idx):
+    from paper_2312_00720_gb300 import gj
+    gj.selector_set(_network_preferring(join_idx, 2), np.zeros(12), np.ones(12))
+    try:
+        for shape in ((1 << 20, 1 << 22, 4, 1, 1, 2, 0.0, 1.0, 1024), (1 << 12, 1 << 16, 8, 2, 2, 4, 1.0, 0.1, 16)):
+            j_plain, g_plain = gj.auto_variants(*shape, selector=1)
+            j_fused, _ = gj.auto_variants(*shape, selector=1, fused=True)
+            assert j_plain == j_fused == 1 + join_idx     # PHJ-TR, PHJ-UR, NPHJ
+            assert g_plain == 3                            # PGB
+            # an explicit variant is never overridden
+            assert gj.auto_variants(*shape, selector=1, fused=True, join="nphj")[0] == 3
+    finally:
+        gj.selector_set(None, None, None)
+
+
+def test_fused_call_follows_the_paper_rule_without_a_network():
+    from paper_2312_00720_gb300 import gj
+    gj.selector_set(None, None, None)
+    for mr, z, kb in ((1.0, 0.0, 4), (0.1, 0.0, 4), (0.1, 0.7, 4), (0.1, 0.0, 8)):
+        shape = (1 << 16, 1 << 18, kb, 2, 2, 2, z, mr, 64)
+        rule = gj.heuristic_choose(*shape)
+        for sel in (0, 1):   # the MLP mode without a network falls back to the rules
+            assert gj.auto_variants(*shape, selector=sel)[0] == rule[0]
+            assert gj.auto_variants(*shape, selector=sel, fused=True)[0] == rule[0]
