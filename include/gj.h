@@ -92,8 +92,11 @@ typedef enum {
 
 typedef enum {
   GJ_GB_AUTO = 0,
-  GJ_GB_HGB = 1, /* hash-based, dense group ids then shared-memory aggregation (Sec. 4.2, Alg. 1) */
-  GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3) */
+  GJ_GB_HGB = 1, /* hash-based, dense group ids then shared-memory aggregation (Sec. 4.2, Alg. 1); its
+                    dictionary table holds 2 x groups_hint entries when a hint is set (a larger group
+                    count gives GJ_ERR_CAPACITY), else 2 x n */
+  GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3), on the key
+                    bits that vary only; synchronises the stream once to read the key range */
   GJ_GB_PGB = 3, /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3) */
   GJ_GB_SGB_UR = 4, /* SGB with (key, tuple id) sorted and values gathered through the ids (GFUR, Sec. 4.1.2) */
   GJ_GB_PGB_UR = 5, /* PGB with (key, tuple id) partitioned and values gathered through the ids (GFUR) */
@@ -115,7 +118,8 @@ typedef struct {
   int32_t reserved;
   float zipf_hint;          /* selector features (negative = unknown) */
   float match_ratio_hint;
-  int64_t groups_hint;      /* expected group count, 0 = unknown */
+  int64_t groups_hint;      /* expected group count, 0 = unknown; sizes HGB's and SGB-DE's dictionary and
+                               PGB's partition count, and is a selector feature */
 } gj_options;
 
 /* Fills *opt with the defaults (AUTO variants, heuristic selector, sync = 0). */

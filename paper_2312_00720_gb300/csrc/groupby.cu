@@ -37,73 +37,139 @@ namespace gj {
 namespace {
 
 // ================================================================ HGB
+// The dictionary (Alg. 1, stage 1): a global open-addressing table of entries
+// (key, g). g = 0 marks an empty slot; kClaim | (row + 1) a slot claimed by the
+// row that is inserting its key; otherwise g - 1 is the key's dense group id,
+// taken from the group counter by the inserting row, which also writes the
+// output key. Stage 2 finds a row's id by looking its key up in this table.
+constexpr uint32_t kClaim = 0x80000000u;
+
 template <typename K>
-__global__ void __launch_bounds__(256) hgb_group_id_kernel(const K* __restrict__ key, int64_t n,
-                                                           int32_t* __restrict__ ht, uint64_t mask,
-                                                           int32_t* __restrict__ gid_of_row,
-                                                           int32_t* __restrict__ gidloc,
-                                                           unsigned long long* ngroups, K* __restrict__ out_keys,
-                                                           int64_t cap, int* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t n_round = (n + 31) & ~int64_t(31);
-  // kBatch rows per thread per step: their key loads and first table probes are
-  // in flight together; a collision continues probing on its own
-  constexpr int kBatch = 4;
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n_round; it += stride * kBatch) {
-    K k[kBatch];
-    bool valid[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int64_t i = it + u * stride;
-      valid[u] = i < n;
-      k[u] = valid[u] ? key[i] : K(0);
-    }
-    int leader[kBatch], prev[kBatch];
-    uint64_t sl[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const unsigned vmask = __ballot_sync(0xffffffffu, valid[u]);
-      const unsigned peers = __match_any_sync(0xffffffffu, k[u]) & vmask;
-      leader[u] = valid[u] ? __ffs(peers) - 1 : lane;
-      sl[u] = KeyTraits<K>::hash64(k[u]) & mask;
-      prev[u] = (valid[u] && lane == leader[u]) ? atomicCAS(&ht[sl[u]], 0, (int)(it + u * stride + 1)) : -1;
-    }
-    K pk[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) pk[u] = prev[u] > 0 ? key[prev[u] - 1] : K(0);
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int64_t i = it + u * stride;
-      int32_t loc = -1;
-      if (prev[u] >= 0) {
-        int pv = prev[u];
-        K pkey = pk[u];
-        uint64_t s2 = sl[u];
-        for (uint64_t probe = 0; probe <= mask; ++probe) {
-          if (pv == 0) {
-            const unsigned long long g = atomicAdd(ngroups, 1ull);
-            gid_of_row[i] = (int32_t)g;
-            if ((int64_t)g < cap)
-              out_keys[g] = k[u];
-            else
-              set_status(err, GJ_ERR_CAPACITY);
-            loc = (int32_t)i;
-            break;
-          }
-          if (pkey == k[u]) {
-            loc = pv - 1;
-            break;
-          }
-          s2 = (s2 + 1) & mask;
-          pv = atomicCAS(&ht[s2], 0, (int)(i + 1));
-          if (pv > 0) pkey = key[pv - 1];
-        }
-        if (loc < 0) set_status(err, GJ_ERR_CAPACITY);  // table full
+struct alignas(2 * sizeof(K)) HEntry {
+  K key;
+  uint32_t g;
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Inserts the key k of row i unless the table holds it already.
+template <typename K>
+__device__ __forceinline__ void hgb_insert(const K* __restrict__ key, HEntry<K>* ht, uint64_t mask, K k, int64_t i,
+                                           unsigned long long* ngroups, K* __restrict__ out_keys, int64_t cap,
+                                           int* err) {
+  uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+  for (uint64_t probe = 0; probe <= mask;) {
+    const uint32_t w = ld_acquire_u32(&ht[sl].g);
+    if (w == 0) {
+      if (atomicCAS(&ht[sl].g, 0u, kClaim | (uint32_t)(i + 1)) == 0u) {
+        ht[sl].key = k;
+        const unsigned long long gid = atomicAdd(ngroups, 1ull);
+        if ((int64_t)gid < cap)
+          out_keys[gid] = k;
+        else
+          set_status(err, GJ_ERR_CAPACITY);
+        st_release_u32(&ht[sl].g, (uint32_t)gid + 1u);  // the key is written before the id is published
+        return;
       }
-      loc = __shfl_sync(0xffffffffu, loc, leader[u]);
-      if (valid[u]) gidloc[i] = loc;
+      continue;  // another row claimed the slot first: read it again
     }
+    const K other = (w & kClaim) ? key[(w & ~kClaim) - 1] : ht[sl].key;
+    if (other == k) return;
+    sl = (sl + 1) & mask;
+    ++probe;
+  }
+  set_status(err, GJ_ERR_CAPACITY);  // the table is full
+}
+
+// Dense group id of key k, or -1 if the table does not hold it. Called after the
+// dictionary kernel has finished, when every entry is final.
+template <typename K>
+__device__ __forceinline__ int32_t hgb_find(const HEntry<K>* __restrict__ ht, uint64_t mask, K k) {
+  uint64_t sl = KeyTraits<K>::hash64(k) & mask;
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    const HEntry<K> e = ht[sl];
+    if (e.g == 0) return -1;
+    if (e.key == k) return (int32_t)(e.g - 1);
+    sl = (sl + 1) & mask;
+  }
+  return -1;
+}
+
+// Keys a block has already inserted or found: a shared-memory set of tagged keys,
+// so that a key repeated across the block's rows reaches the global table once per
+// block. 4-byte keys are tagged with bit 32 (empty = 0); 8-byte keys are stored as
+// they are (empty = INT64_MIN, a key of that value is simply never cached).
+constexpr int kSeenSlots = 4096;
+constexpr int kSeenProbes = 4;
+template <typename K>
+__device__ __forceinline__ unsigned long long seen_tag(K k) {
+  return sizeof(K) == 4 ? ((1ull << 32) | (uint64_t)(uint32_t)k) : (unsigned long long)(int64_t)k;
+}
+template <typename K>
+__device__ __forceinline__ unsigned long long seen_empty() {
+  return sizeof(K) == 4 ? 0ull : 0x8000000000000000ull;
+}
+
+// Stage 1: build the dictionary. Writes nothing per row.
+template <typename K>
+__global__ void __launch_bounds__(512) hgb_dict_kernel(const K* __restrict__ key, int64_t n, HEntry<K>* ht,
+                                                       uint64_t mask, unsigned long long* ngroups,
+                                                       K* __restrict__ out_keys, int64_t cap, int* err) {
+  __shared__ unsigned long long s_seen[kSeenSlots];
+  const unsigned long long empty = seen_empty<K>();
+  for (int j = threadIdx.x; j < kSeenSlots; j += blockDim.x) s_seen[j] = empty;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int kBatch = 4;  // rows per thread per step: their key loads are in flight together
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n; it += stride * kBatch) {
+    K kk[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = it + u * stride;
+      kk[u] = i < n ? __ldcs(key + i) : K(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = it + u * stride;
+      if (i >= n) continue;
+      const unsigned long long tag = seen_tag<K>(kk[u]);
+      bool handled = false;
+      if (tag != empty) {
+        uint32_t s = (uint32_t)KeyTraits<K>::hash64(kk[u]) & (kSeenSlots - 1);
+        for (int p = 0; p < kSeenProbes; ++p) {
+          unsigned long long v = s_seen[s];
+          if (v == empty) {
+            v = atomicCAS(&s_seen[s], empty, tag);
+            if (v == empty) break;  // this row inserts the key on the block's behalf
+          }
+          if (v == tag) {
+            handled = true;  // another row of the block has inserted or found it
+            break;
+          }
+          s = (s + 1) & (kSeenSlots - 1);
+        }
+      }
+      if (!handled) hgb_insert<K>(key, ht, mask, kk[u], i, ngroups, out_keys, cap, err);
+    }
+  }
+}
+
+// code[i] = the dense group id of row i: the dictionary code SGB-DE sorts.
+template <typename K>
+__global__ void hgb_codes_kernel(const K* __restrict__ key, int64_t n, const HEntry<K>* __restrict__ ht,
+                                 uint64_t mask, int32_t* __restrict__ code, int* err) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int32_t g = hgb_find<K>(ht, mask, __ldcs(key + i));
+    if (g < 0) set_status(err, GJ_ERR_CAPACITY);  // its insert failed and was reported
+    code[i] = g < 0 ? 0 : g;
   }
 }
 
@@ -136,11 +202,12 @@ struct SmemAggLayout {
   int32_t bytes_per_group;
 };
 
+// Adds v (for COUNT: a count of rows) into one shared-memory slot.
 __device__ __forceinline__ void smem_update(int op, int width, unsigned char* slot, int64_t v) {
   if (width == 8) {
     agg_atomic(op, (int64_t*)slot, v);
   } else if (op == GJ_AGG_COUNT) {
-    atomicAdd((unsigned int*)slot, 1u);
+    atomicAdd((unsigned int*)slot, (unsigned int)v);
   } else if (op == GJ_AGG_MIN) {
     atomicMin((int*)slot, (int)v);
   } else {
@@ -163,88 +230,134 @@ __device__ __forceinline__ void smem_init(int op, int width, unsigned char* slot
     *(int*)slot = op == GJ_AGG_MIN ? INT32_MAX : INT32_MIN;
 }
 
-__global__ void __launch_bounds__(1024) hgb_agg_kernel(const int32_t* __restrict__ gidloc,
-                                                       const int32_t* __restrict__ gid_of_row, int64_t n, Aggs A,
-                                                       ColCache cc, SmemAggLayout L, const int64_t* __restrict__ ngroups,
-                                                       int64_t cap, int smem_budget) {
+// One warp-wide step of an aggregation: every lane holds one row (ok = it takes
+// part, gid its group, cv its cached 4-byte values at position u). Lanes of equal
+// gid are combined first (match.any, then redux.sync: COUNT is the peer count,
+// SUM adds the high and low 16-bit halves separately so 32 values never overflow,
+// MIN/MAX directly) and only the lowest lane of each group calls update(j, gid, v);
+// when the step holds no repeated group every lane updates for itself. Aggregates
+// over columns outside the cache are never combined.
+template <int B, typename Update>
+__device__ __forceinline__ void warp_aggregate(const Aggs& A, const ColCache& cc, bool ok, int32_t gid,
+                                               const int32_t (&cv)[kColCache][B], int u, int64_t row,
+                                               Update&& update) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, ok ? gid : -1 - lane);
+  if (!__any_sync(0xffffffffu, __popc(peers) > 1)) {
+    if (ok)
+      for (int j = 0; j < A.n; ++j) update(j, gid, cached_value<B>(A, cc, j, cv, u, row));
+    return;
+  }
+  const bool leader = ok && lane == __ffs(peers) - 1;
+  for (int j = 0; j < A.n; ++j) {
+    const int op = A.op[j];
+    const int s = cc.slot[j];
+    int64_t v;
+    if (op == GJ_AGG_COUNT) {
+      v = __popc(peers);
+    } else if (s >= 0) {
+      const int32_t x = s == 0 ? cv[0][u] : (s == 1 ? cv[1][u] : cv[2][u]);
+      if (op == GJ_AGG_SUM) {
+        const int hi = __reduce_add_sync(peers, x >> 16);
+        const unsigned lo = __reduce_add_sync(peers, (unsigned)(x & 0xffff));
+        v = (int64_t)hi * 65536 + (int64_t)lo;
+      } else if (op == GJ_AGG_MIN) {
+        v = __reduce_min_sync(peers, x);
+      } else {
+        v = __reduce_max_sync(peers, x);
+      }
+    } else {
+      if (ok) update(j, gid, cached_value<B>(A, cc, j, cv, u, row));
+      continue;
+    }
+    if (leader) update(j, gid, v);
+  }
+}
+
+// Stage 2: every row's group id from the dictionary, then its aggregates. When
+// the g groups' slots fit in shared memory (is_smem_enough, decided here on the
+// device from the group counter) each block aggregates into shared memory --
+// one copy per warp, or per few warps, when several copies fit, so warps do not
+// contend for the same slots -- and adds its slots into the result at the end;
+// otherwise rows are aggregated straight into the result with global atomics.
+template <typename K>
+__global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restrict__ key, int64_t n,
+                                                                const HEntry<K>* __restrict__ ht, uint64_t mask,
+                                                                Aggs A, ColCache cc, SmemAggLayout L,
+                                                                const int64_t* __restrict__ ngroups, int64_t cap,
+                                                                int smem_budget, int* err) {
   extern __shared__ __align__(16) unsigned char s_agg[];
   const int64_t g = min64(*ngroups, cap);
-  const bool use_smem = g * (int64_t)L.bytes_per_group <= smem_budget;  // is_smem_enough
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (use_smem) {
-    int64_t offs[kMaxAggs];
+  const int64_t copy_bytes = (g * (int64_t)L.bytes_per_group + 15) & ~int64_t(15);
+  const bool use_smem = copy_bytes <= smem_budget;  // is_smem_enough
+  const int nwarps = blockDim.x >> 5;
+  int ncopy = 1;
+  while (use_smem && ncopy < nwarps && 2 * ncopy * copy_bytes <= smem_budget) ncopy *= 2;
+  const int warp = threadIdx.x >> 5;
+  __shared__ int64_t offs[kMaxAggs];  // aggregate j's slot array within a copy
+  if (threadIdx.x == 0) {
     int64_t o = 0;
     for (int q = 0; q < A.n; ++q) {
-      int j = L.order[q];
+      const int j = L.order[q];
       offs[j] = o;
       o += g * L.width[j];
     }
-    for (int q = 0; q < A.n; ++q) {
-      int j = L.order[q];
-      for (int64_t s = threadIdx.x; s < g; s += blockDim.x) smem_init(A.op[j], L.width[j], s_agg + offs[j] + s * L.width[j]);
-    }
+  }
+  __syncthreads();
+  if (use_smem) {
+    for (int c = 0; c < ncopy; ++c)
+      for (int q = 0; q < A.n; ++q) {
+        const int j = L.order[q];
+        for (int64_t s = threadIdx.x; s < g; s += blockDim.x)
+          smem_init(A.op[j], L.width[j], s_agg + c * copy_bytes + offs[j] + s * L.width[j]);
+      }
     __syncthreads();
-    // kBatch rows per thread per step: dependent loads of the batch overlap
-    constexpr int kBatch = 4;
-    for (int64_t it = first; it < n; it += stride * kBatch) {
-      int32_t loc[kBatch];
-      int64_t gid[kBatch];
+  }
+  unsigned char* mine = s_agg + (warp & (ncopy - 1)) * copy_bytes;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int kBatch = 4;  // rows per thread per step: loads and lookups of the batch overlap
+  bool lost = false;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it - threadIdx.x < n; it += stride * kBatch) {
+    int64_t row[kBatch];
+    bool valid[kBatch];
+    K kk[kBatch];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) loc[u] = it + u * stride < n ? gidloc[it + u * stride] : -1;
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) gid[u] = loc[u] >= 0 ? gid_of_row[loc[u]] : g;  // < 0: insert failed
-      int64_t row[kBatch];
-      bool valid[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        row[u] = it + u * stride;
-        valid[u] = gid[u] < g;
-      }
-      int32_t cv[kColCache][kBatch];
-      load_cached<kBatch>(cc, row, valid, cv);
-      for (int j = 0; j < A.n; ++j) {
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-          if (valid[u])
-            smem_update(A.op[j], L.width[j], s_agg + offs[j] + gid[u] * L.width[j],
-                        cached_value<kBatch>(A, cc, j, cv, u, row[u]));
-      }
+    for (int u = 0; u < kBatch; ++u) {
+      row[u] = it + u * stride;
+      valid[u] = row[u] < n;
+      kk[u] = valid[u] ? __ldcs(key + row[u]) : K(0);
     }
-    __syncthreads();
-    for (int j = 0; j < A.n; ++j) {
-      const int64_t idv = agg_identity(A.op[j]);
-      for (int64_t s = threadIdx.x; s < g; s += blockDim.x) {
-        int64_t v = smem_read(A.op[j], L.width[j], s_agg + offs[j] + s * L.width[j]);
-        if (L.width[j] == 4 && A.op[j] == GJ_AGG_MIN && v == INT32_MAX) continue;
-        if (L.width[j] == 4 && A.op[j] == GJ_AGG_MAX && v == INT32_MIN) continue;
-        if (v == idv) continue;
-        agg_atomic(A.op[j], &A.out[j][s], v);
-      }
+    int32_t gid[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) gid[u] = valid[u] ? hgb_find<K>(ht, mask, kk[u]) : -1;
+    int32_t cv[kColCache][kBatch];
+    load_cached<kBatch>(cc, row, valid, cv);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      lost |= valid[u] && gid[u] < 0;
+      const bool ok = valid[u] && gid[u] >= 0 && gid[u] < g;
+      if (use_smem)
+        warp_aggregate<kBatch>(A, cc, ok, gid[u], cv, u, row[u], [&](int j, int32_t gr, int64_t v) {
+          smem_update(A.op[j], L.width[j], mine + offs[j] + (int64_t)gr * L.width[j], v);
+        });
+      else
+        warp_aggregate<kBatch>(A, cc, ok, gid[u], cv, u, row[u],
+                               [&](int j, int32_t gr, int64_t v) { agg_atomic(A.op[j], &A.out[j][gr], v); });
     }
-  } else {
-    constexpr int kBatch = 4;
-    for (int64_t it = first; it < n; it += stride * kBatch) {
-      int32_t loc[kBatch];
-      int64_t gid[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) loc[u] = it + u * stride < n ? gidloc[it + u * stride] : -1;
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) gid[u] = loc[u] >= 0 ? gid_of_row[loc[u]] : g;
-      int64_t row[kBatch];
-      bool valid[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        row[u] = it + u * stride;
-        valid[u] = gid[u] < g;
-      }
-      int32_t cv[kColCache][kBatch];
-      load_cached<kBatch>(cc, row, valid, cv);
-      for (int j = 0; j < A.n; ++j) {
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-          if (valid[u]) agg_atomic(A.op[j], &A.out[j][gid[u]], cached_value<kBatch>(A, cc, j, cv, u, row[u]));
-      }
+  }
+  if (lost) set_status(err, GJ_ERR_CAPACITY);  // a key whose insert failed (reported by stage 1)
+  if (!use_smem) return;
+  __syncthreads();
+  for (int j = 0; j < A.n; ++j) {
+    const int op = A.op[j], w = L.width[j];
+    const int64_t idv = agg_identity(op);
+    for (int64_t s = threadIdx.x; s < g; s += blockDim.x) {
+      int64_t v = smem_read(op, w, s_agg + offs[j] + s * w);
+      for (int c = 1; c < ncopy; ++c) v = agg_combine(op, v, smem_read(op, w, s_agg + c * copy_bytes + offs[j] + s * w));
+      if (w == 4 && op == GJ_AGG_MIN && v == INT32_MAX) continue;
+      if (w == 4 && op == GJ_AGG_MAX && v == INT32_MIN) continue;
+      if (v == idv) continue;
+      agg_atomic(op, &A.out[j][s], v);
     }
   }
 }
@@ -684,10 +797,19 @@ __global__ void __launch_bounds__(kSegWarps * 32, 2) sgb_reduce_kernel(const K* 
 }
 
 // ================================================================ PGB
+// One block per partition (Sec. 4.3). The block inserts the partition's keys into
+// a shared-memory table sized to the partition (a slot holds the partition row +
+// 1 of its key's first row; keys are compared in global memory, where the small
+// partition stays cached), gives the keys dense local ids in slot order,
+// aggregates every row into shared-memory slots by local id (warp_aggregate:
+// rows of one key in a warp are combined before the atomics), then reserves its
+// output rows from the global group counter and writes them with plain stores.
+// A partition whose distinct keys exceed the block's group capacity C is split by
+// a second hash into two halves, recursively, each processed as above.
 constexpr int kPgbThreads = 512;
-constexpr int kPgbCap = 4096;        // distinct keys per shared-memory table
-constexpr int kPgbSlots = 2 * kPgbCap;
 constexpr int kPgbMaxQ = 12;
+constexpr int kPgbSmem = 110 * 1024;  // dynamic shared memory budget of a block (two blocks per SM)
+constexpr int kPgbMaxCap = 4096;      // groups per round (local ids fit int16)
 
 template <typename K>
 __device__ __forceinline__ uint32_t pgb_sub(K k, int q) {
@@ -697,374 +819,225 @@ __device__ __forceinline__ uint32_t pgb_sub(K k, int q) {
 }
 
 template <typename K>
-__device__ __forceinline__ uint32_t pgb_slot(K k, int pbits) {
-  return (uint32_t)(KeyTraits<K>::hash64(k) >> pbits) & (kPgbSlots - 1);
+__device__ __forceinline__ uint32_t pgb_slot(K k, int pbits, int tslots) {
+  return (uint32_t)(KeyTraits<K>::hash64(k) >> pbits) & (uint32_t)(tslots - 1);
 }
 
-// Inserts the keys of rows [r0, r1) with sub-round `round` into the table.
-// Returns the distinct count, or -1 on overflow.
-// Inserts the keys of rows [r0, r1) with sub-round `round` into the table. A
-// slot holds (partition row + 1) of the first row seen with its key; keys are
-// compared in global memory, so claiming a slot is one CAS and no thread ever
-// waits on another. Occupied slots then get dense local ids in slot order
-// (s_keys[lid], s_lid[slot]). Returns the distinct count, or -1 if it exceeds
-// kPgbCap.
+// Dynamic shared memory of a PGB block with group capacity C: table (2C int32
+// slots, 2C int16 local ids), keys by local id, then the aggregate arrays.
 template <typename K>
-__device__ int pgb_build(const K* __restrict__ key, int64_t r0, int64_t r1, int q, uint32_t round, int pbits,
-                         int32_t* s_slots, K* s_keys, int* s_count, int* s_over) {
-  int16_t* s_lid = (int16_t*)(s_keys + kPgbCap);
-  for (int j = threadIdx.x; j < kPgbSlots; j += blockDim.x) s_slots[j] = 0;
-  if (threadIdx.x == 0) {
-    *s_count = 0;
-    *s_over = 0;
-  }
-  __syncthreads();
-  // rows in batches of kBatch per thread: the batch's key loads are in flight together
-  constexpr int kBatch = 8;
-  // the last key this thread inserted or found: a run of equal keys (few groups
-  // per partition) skips the table after its first row
-  K last = K(0);
-  bool has_last = false;
-  for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
-    K kk[kBatch];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
-      kk[u] = i < r1 ? key[i] : K(0);
-    }
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
-      if (i >= r1) continue;
-      const K k = kk[u];
-      if (has_last && k == last) continue;
-      if (pgb_sub<K>(k, q) != round) continue;
-      last = k;
-      has_last = true;
-      uint32_t sl = pgb_slot<K>(k, pbits);
-      volatile int32_t* vs = s_slots;
-      for (int probe = 0; probe < kPgbSlots; ++probe) {
-        int v = vs[sl];  // a repeated key finds its slot without an atomic
-        if (v == 0) {
-          v = atomicCAS(&s_slots[sl], 0, (int)(i - r0 + 1));
-          if (v == 0) break;
-        }
-        if (key[r0 + v - 1] == k) break;
-        sl = (sl + 1) & (kPgbSlots - 1);
-      }
-    }
-  }
-  __syncthreads();
-  // dense ids in slot order: block-wide count of occupied slots before each one
-  constexpr int kPer = kPgbSlots / kPgbThreads;
-  const int s0 = threadIdx.x * kPer;
-  int mine = 0;
-#pragma unroll
-  for (int r = 0; r < kPer; ++r) mine += s_slots[s0 + r] != 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  __shared__ int s_wsum[kPgbThreads / 32];
-  if (lane == 31) s_wsum[warp] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int w = 0; w < kPgbThreads / 32; ++w) {
-      const int c = s_wsum[w];
-      s_wsum[w] = run;
-      run += c;
-    }
-    *s_count = run;
-    *s_over = run > kPgbCap;
-  }
-  __syncthreads();
-  const int total = *s_count;
-  if (total <= kPgbCap) {
-    int lid = s_wsum[warp] + x - mine;
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int v = s_slots[s0 + r];
-      if (v != 0) {
-        s_keys[lid] = key[r0 + v - 1];
-        s_lid[s0 + r] = (int16_t)lid;
-        ++lid;
-      }
-    }
-  }
-  __syncthreads();
-  return total > kPgbCap ? -1 : total;
+__host__ __device__ constexpr int pgb_key_off(int C) {
+  return (C * 2 * 4 + C * 2 * 2 + 15) & ~15;
 }
-
 template <typename K>
-__device__ __forceinline__ int pgb_lookup(K k, int pbits, const int32_t* s_slots, const K* s_keys) {
-  const int16_t* s_lid = (const int16_t*)(s_keys + kPgbCap);
-  uint32_t sl = pgb_slot<K>(k, pbits);
-  for (int probe = 0; probe < kPgbSlots; ++probe) {
-    const int v = s_slots[sl];
-    if (v == 0) return -1;
-    const int l = s_lid[sl];
-    if (s_keys[l] == k) return l;
-    sl = (sl + 1) & (kPgbSlots - 1);
-  }
-  return -1;
+__host__ __device__ constexpr int pgb_agg_off(int C) {
+  return (pgb_key_off<K>(C) + C * (int)sizeof(K) + 15) & ~15;
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict__ key,
                                                           const int64_t* __restrict__ poff, int pbits, Aggs A,
-                                                          ColCache cc, K* __restrict__ out_keys, int64_t cap, int mode,
-                                                          int64_t* __restrict__ gcount, int8_t* __restrict__ qsel,
-                                                          int* err) {
+                                                          ColCache cc, SmemAggLayout L, int C,
+                                                          K* __restrict__ out_keys, int64_t cap,
+                                                          unsigned long long* ngroups, int* err) {
   extern __shared__ __align__(16) unsigned char s_raw[];
-  int64_t* s_agg = (int64_t*)s_raw;                       // kPgbCap aggregates
-  int32_t* s_slots = (int32_t*)(s_agg + kPgbCap);         // table: local id + 1
-  K* s_keys = (K*)(s_slots + kPgbSlots);                  // distinct keys by local id
-  __shared__ int s_count, s_over;
-  __shared__ int64_t s_red[kPgbThreads / 32];
+  int32_t* s_slot = (int32_t*)s_raw;
+  int16_t* s_lid = (int16_t*)(s_slot + 2 * C);
+  K* s_key = (K*)(s_raw + pgb_key_off<K>(C));
+  unsigned char* s_agg = s_raw + pgb_agg_off<K>(C);
+  __shared__ int64_t offs[kMaxAggs];
+  __shared__ int s_wsum[kPgbThreads / 32];
+  __shared__ int s_count;
+  __shared__ unsigned long long s_base;
+  __shared__ int s_stack_q[kPgbMaxQ + 2];
+  __shared__ uint32_t s_stack_r[kPgbMaxQ + 2];
+  __shared__ int s_top;
 
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = blockIdx.x;
   const int64_t r0 = poff[p], r1 = poff[p + 1];
-
-  int q = 0;
-  int64_t total = 0;
-  if (mode == 0) {
-    // ---- counting launch: the smallest split q whose sub-rounds all fit
-    for (;;) {
-      total = 0;
-      bool ok = true;
-      for (uint32_t round = 0; round < (1u << q); ++round) {
-        int c = pgb_build<K>(key, r0, r1, q, round, pbits, s_slots, s_keys, &s_count, &s_over);
-        if (c < 0) {
-          ok = false;
-          break;
-        }
-        total += c;
-      }
-      __syncthreads();
-      if (ok) break;
-      if (++q > kPgbMaxQ) {
-        if (threadIdx.x == 0) set_status(err, GJ_ERR_CAPACITY);
-        total = 0;
-        q = -1;
-        break;
-      }
+  if (r1 <= r0) return;
+  const int64_t rows = r1 - r0;
+  int tslots = 64;  // table slots: about twice the rows, at most 2C
+  while (tslots < 2 * C && tslots < 2 * rows) tslots <<= 1;
+  if (tid == 0) {
+    int64_t o = 0;
+    for (int q = 0; q < A.n; ++q) {
+      const int j = L.order[q];
+      offs[j] = o;
+      o += (int64_t)C * L.width[j];
     }
-    if (threadIdx.x == 0) {
-      gcount[p] = total;
-      qsel[p] = (int8_t)q;
-    }
-    return;
+    s_stack_q[0] = 0;
+    s_stack_r[0] = 0;
+    s_top = 1;
   }
-  // ---- aggregating launch: offsets are known, no block waits on another
-  q = qsel[p];
-  if (q < 0) return;
-  const int64_t goff = gcount[p];
-  total = gcount[p + 1] - goff;
-  if (total == 0) return;
-  // one group needs no table: every row of the partition holds the key of its first
-  if (q == 0 && total > 1) pgb_build<K>(key, r0, r1, 0, 0, pbits, s_slots, s_keys, &s_count, &s_over);
-
-  // one group: register accumulators below
-  constexpr int kOneGroupAggs = 8;
-  const bool one_group = q == 0 && total == 1;
-
-  // ---- few groups, one round: every aggregate in one pass over the partition.
-  // When the slots are few, every warp updates its own copy (no contention
-  // between warps) and the copies are combined at the end.
-  if (q == 0 && !one_group && total * A.n <= kPgbCap) {
-    const int g = (int)total;
-    const int nsl = g * A.n;
-    constexpr int kWarpsPgb = kPgbThreads / 32;
-    const int ncopy = nsl * kWarpsPgb <= kPgbCap ? kWarpsPgb : 1;
-    int64_t* my = s_agg + (ncopy > 1 ? (threadIdx.x >> 5) * nsl : 0);
-    for (int l = threadIdx.x; l < g; l += blockDim.x) {
-      if (goff + l < cap)
-        out_keys[goff + l] = s_keys[l];
-      else
-        set_status(err, GJ_ERR_CAPACITY);
-    }
-    for (int s = threadIdx.x; s < nsl * ncopy; s += blockDim.x) s_agg[s] = agg_identity(A.op[(s % nsl) / g]);
+  __syncthreads();
+  bool over_cap = false;
+  // rounds (q, r): the rows whose second hash has r in its low q bits
+  while (s_top > 0) {
+    const int q = s_stack_q[s_top - 1];
+    const uint32_t round = s_stack_r[s_top - 1];
     __syncthreads();
+    if (tid == 0) {
+      --s_top;
+      s_count = 0;
+    }
+    for (int j = tid; j < tslots; j += blockDim.x) s_slot[j] = 0;
+    __syncthreads();
+    // ---- insert the round's keys
     constexpr int kBatch = 4;
     for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
       K kk[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        const int64_t i = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+        const int64_t i = b0 + (int64_t)u * blockDim.x + tid;
         kk[u] = i < r1 ? key[i] : K(0);
       }
-      int lid[kBatch];
-      int64_t row[kBatch];
-      bool valid[kBatch];
 #pragma unroll
       for (int u = 0; u < kBatch; ++u) {
-        row[u] = b0 + (int64_t)u * blockDim.x + threadIdx.x;
+        const int64_t i = b0 + (int64_t)u * blockDim.x + tid;
+        if (i >= r1 || pgb_sub<K>(kk[u], q) != round) continue;
+        uint32_t sl = pgb_slot<K>(kk[u], pbits, tslots);
+        for (int probe = 0; probe < tslots; ++probe) {
+          int v = ((volatile int32_t*)s_slot)[sl];  // a repeated key finds its slot without an atomic
+          if (v == 0) {
+            v = atomicCAS(&s_slot[sl], 0, (int)(i - r0 + 1));
+            if (v == 0) break;
+          }
+          if (key[r0 + v - 1] == kk[u]) break;
+          sl = (sl + 1) & (uint32_t)(tslots - 1);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- dense local ids in slot order
+    const int per = (tslots + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min(tid * per, tslots), s1 = min(s0 + per, tslots);
+    int mine = 0;
+    for (int j = s0; j < s1; ++j) mine += s_slot[j] != 0;
+    int x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int c = s_wsum[w];
+        s_wsum[w] = run;
+        run += c;
+      }
+      s_count = run;
+    }
+    __syncthreads();
+    const int count = s_count;
+    if (count > C) {
+      // too many keys for one round: split it by the next bit of the second hash
+      if (tid == 0) {
+        if (q < kPgbMaxQ) {
+          s_stack_q[s_top] = q + 1;
+          s_stack_r[s_top] = round | (1u << q);
+          s_stack_q[s_top + 1] = q + 1;
+          s_stack_r[s_top + 1] = round;
+          s_top += 2;
+        } else {
+          set_status(err, GJ_ERR_CAPACITY);
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+    {
+      int lid = s_wsum[warp] + x - mine;
+      for (int j = s0; j < s1; ++j) {
+        const int v = s_slot[j];
+        if (v != 0) {
+          s_key[lid] = key[r0 + v - 1];
+          s_lid[j] = (int16_t)lid;
+          ++lid;
+        }
+      }
+    }
+    for (int jq = 0; jq < A.n; ++jq)
+      for (int l = tid; l < count; l += blockDim.x)
+        smem_init(A.op[jq], L.width[jq], s_agg + offs[jq] + (int64_t)l * L.width[jq]);
+    __syncthreads();
+    // ---- aggregate the round's rows by local id (the loop bound is uniform:
+    // warp_aggregate needs every lane of the warp)
+    for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
+      int64_t row[kBatch];
+      bool valid[kBatch];
+      int32_t lid[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        row[u] = b0 + (int64_t)u * blockDim.x + tid;
         valid[u] = row[u] < r1;
-        lid[u] = valid[u] ? pgb_lookup<K>(kk[u], pbits, s_slots, s_keys) : -1;
+        lid[u] = -1;
+        if (!valid[u]) continue;
+        const K k = key[row[u]];
+        if (pgb_sub<K>(k, q) != round) continue;
+        uint32_t sl = pgb_slot<K>(k, pbits, tslots);
+        for (int probe = 0; probe < tslots; ++probe) {
+          if (s_slot[sl] == 0) break;
+          const int l = s_lid[sl];
+          if (s_key[l] == k) {
+            lid[u] = l;
+            break;
+          }
+          sl = (sl + 1) & (uint32_t)(tslots - 1);
+        }
       }
       int32_t cv[kColCache][kBatch];
       load_cached<kBatch>(cc, row, valid, cv);
-      for (int j = 0; j < A.n; ++j) {
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-          if (lid[u] >= 0) agg_atomic(A.op[j], &my[j * g + lid[u]], cached_value<kBatch>(A, cc, j, cv, u, row[u]));
-      }
+      for (int u = 0; u < kBatch; ++u)
+        warp_aggregate<kBatch>(A, cc, lid[u] >= 0, lid[u], cv, u, row[u], [&](int j, int32_t l, int64_t v) {
+          smem_update(A.op[j], L.width[j], s_agg + offs[j] + (int64_t)l * L.width[j], v);
+        });
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < nsl; s += blockDim.x) {
-      const int j = s / g, l = s - j * g;
-      int64_t v = s_agg[s];
-      for (int c = 1; c < ncopy; ++c) v = agg_combine(A.op[j], v, s_agg[c * nsl + s]);
-      if (goff + l < cap) A.out[j][goff + l] = v;
-    }
-    return;
-  }
-
-  // ---- one group: aggregates accumulated in registers, kOneGroupAggs per pass
-  // over the partition, then a block-wide reduction (no atomics)
-  if (one_group) {
-    if (threadIdx.x == 0) {
-      if (goff < cap)
-        out_keys[goff] = key[r0];
-      else
-        set_status(err, GJ_ERR_CAPACITY);
-    }
-    for (int j0 = 0; j0 < A.n; j0 += kOneGroupAggs) {
-      int64_t acc[kOneGroupAggs];
-#pragma unroll
-      for (int j = 0; j < kOneGroupAggs; ++j) acc[j] = j0 + j < A.n ? agg_identity(A.op[j0 + j]) : 0;
-      constexpr int kBatch = 4;
-      for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
-        int64_t row[kBatch];
-        bool valid[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          row[u] = b0 + (int64_t)u * blockDim.x + threadIdx.x;
-          valid[u] = row[u] < r1;
-        }
-        int32_t cv[kColCache][kBatch];
-        load_cached<kBatch>(cc, row, valid, cv);
-#pragma unroll
-        for (int j = 0; j < kOneGroupAggs; ++j) {
-          if (j0 + j < A.n) {
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u)
-              if (valid[u])
-                acc[j] = agg_combine(A.op[j0 + j], acc[j], cached_value<kBatch>(A, cc, j0 + j, cv, u, row[u]));
-          }
-        }
+    // ---- the round's groups: output rows reserved from the global counter
+    if (tid == 0) s_base = atomicAdd(ngroups, (unsigned long long)count);
+    __syncthreads();
+    for (int l = tid; l < count; l += blockDim.x) {
+      const int64_t o = (int64_t)s_base + l;
+      if (o >= cap) {
+        over_cap = true;
+        continue;
       }
-#pragma unroll
-      for (int j = 0; j < kOneGroupAggs; ++j) {
-        if (j0 + j >= A.n) break;
-        for (int o = 16; o > 0; o >>= 1)
-          acc[j] = agg_combine(A.op[j0 + j], acc[j], __shfl_down_sync(0xffffffffu, acc[j], o));
-        if ((threadIdx.x & 31) == 0) s_agg[(threadIdx.x >> 5) * kOneGroupAggs + j] = acc[j];
-      }
-      __syncthreads();
-      if (threadIdx.x < kOneGroupAggs && j0 + (int)threadIdx.x < A.n && goff < cap) {
-        const int j = j0 + threadIdx.x;
-        int64_t t = s_agg[threadIdx.x];
-        for (int w = 1; w < kPgbThreads / 32; ++w) t = agg_combine(A.op[j], t, s_agg[w * kOneGroupAggs + threadIdx.x]);
-        A.out[j][goff] = t;
-      }
-      __syncthreads();
+      out_keys[o] = s_key[l];
+      for (int j = 0; j < A.n; ++j) A.out[j][o] = smem_read(A.op[j], L.width[j], s_agg + offs[j] + (int64_t)l * L.width[j]);
     }
-    return;
-  }
-
-  int64_t base = goff;
-  for (uint32_t round = 0; round < (1u << q); ++round) {
-    // with one round the table built during discovery is still in place
-    int g = q == 0 ? (int)total : pgb_build<K>(key, r0, r1, q, round, pbits, s_slots, s_keys, &s_count, &s_over);
-    if (g <= 0) continue;
-    for (int l = threadIdx.x; l < g; l += blockDim.x) {
-      if (base + l < cap)
-        out_keys[base + l] = s_keys[l];
-      else
-        set_status(err, GJ_ERR_CAPACITY);
-    }
-    for (int j = 0; j < A.n; ++j) {
-      const int op = A.op[j];
-      if (g == 1) {
-        // one group: block-wide reduction, no atomics
-        int64_t acc = agg_identity(op);
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
-          if (pgb_sub<K>(key[i], q) == round) acc = agg_combine(op, acc, agg_value(A, j, i));
-        for (int o = 16; o > 0; o >>= 1) acc = agg_combine(op, acc, __shfl_down_sync(0xffffffffu, acc, o));
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          int64_t t = s_red[0];
-          for (int w = 1; w < kPgbThreads / 32; ++w) t = agg_combine(op, t, s_red[w]);
-          if (base < cap) A.out[j][base] = t;
-        }
-        __syncthreads();
-      } else {
-        for (int l = threadIdx.x; l < g; l += blockDim.x) s_agg[l] = agg_identity(op);
-        __syncthreads();
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-          K k = key[i];
-          if (pgb_sub<K>(k, q) != round) continue;
-          int lid = pgb_lookup<K>(k, pbits, s_slots, s_keys);
-          if (lid >= 0) agg_atomic(op, &s_agg[lid], agg_value(A, j, i));
-        }
-        __syncthreads();
-        for (int l = threadIdx.x; l < g; l += blockDim.x)
-          if (base + l < cap) A.out[j][base + l] = s_agg[l];
-        __syncthreads();
-      }
-    }
-    base += g;
     __syncthreads();
   }
+  if (over_cap) set_status(err, GJ_ERR_CAPACITY);
 }
 
-// In-place exclusive scan of v[0..n) (n <= 2^20) by one block; v[n] and *total
-// receive the sum.
-__global__ void __launch_bounds__(1024) excl_scan_kernel(int64_t* v, int64_t n, int64_t* total) {
-  __shared__ int64_t s_w[32];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int64_t per = (n + 1023) / 1024;
-  const int64_t b = (int64_t)t * per, e = min64(n, b + per);
-  int64_t sum = 0;
-  for (int64_t i = b; i < e; ++i) sum += v[i];
-  int64_t x = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int64_t w = s_w[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    s_w[lane] = w;
-  }
-  __syncthreads();
-  int64_t run = (warp ? s_w[warp - 1] : 0) + x - sum;
-  for (int64_t i = b; i < e; ++i) {
-    const int64_t c = v[i];
-    v[i] = run;
-    run += c;
-  }
-  if (t == 1023) {
-    v[n] = run;
-    *total = run;
-  }
-}
-
+// Smallest and largest signed-order bit pattern of the keys: mm[0] = min, mm[1] =
+// max (mm starts at {~0, 0}).
 template <typename K>
-constexpr size_t pgb_smem_bytes() {
-  // aggregates, slots, keys by local id, local id by slot
-  return (size_t)kPgbCap * 8 + (size_t)kPgbSlots * 4 + (size_t)kPgbCap * sizeof(K) + (size_t)kPgbSlots * 2;
+__global__ void __launch_bounds__(256) key_range_kernel(const K* __restrict__ key, int64_t n,
+                                                         unsigned long long* mm) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long u = (unsigned long long)digit_source<K>(__ldcs(key + i), kSignedOrder);
+    lo = u < lo ? u : lo;
+    hi = u > hi ? u : hi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&mm[0], lo);
+    atomicMax(&mm[1], hi);
+  }
 }
 
 // ================================================================ host
@@ -1139,17 +1112,6 @@ gj_status sgb_reduce_run(const Ctx& ctx, Scratch& scr, const K* k2, int64_t n, c
   return cuda_check(cudaGetLastError());
 }
 
-// code[i] = the dense group id of row i (HGB stage 1: gid_of_row at the row its key
-// was inserted with), the dictionary code SGB-DE sorts.
-__global__ void de_codes_kernel(const int32_t* __restrict__ gidloc, const int32_t* __restrict__ gid_of_row, int64_t n,
-                                int32_t* __restrict__ code) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int32_t loc = gidloc[i];
-    code[i] = loc >= 0 ? gid_of_row[loc] : 0;  // a failed insert has set the status already
-  }
-}
-
 template <typename K>
 gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int32_t* ops, const int32_t* op_col,
                         const gj_options* opt, int variant, void* out_keys, int64_t* const* out_aggs, int64_t cap,
@@ -1161,23 +1123,26 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   if ((st = cuda_check(cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), s))) != GJ_OK) return st;
   if (n == 0) return GJ_OK;
 
-  if (variant == GJ_GB_HGB) {
-    uint64_t want = (uint64_t)std::max<int64_t>(2, 2 * (opt->groups_hint > 0 ? std::min(opt->groups_hint, n) : n));
-    uint64_t slots = 1;
+  // HGB and SGB-DE share the dictionary of Alg. 1, stage 1: a table of (key, dense
+  // id) entries sized for twice the expected groups (the hint, else n), filled
+  // by one pass over the keys; out_keys receives the dictionary (id -> key).
+  HEntry<K>* ht = nullptr;
+  uint64_t slots = 1;
+  if (variant == GJ_GB_HGB || variant == GJ_GB_SGB_DE) {
+    const uint64_t want =
+        (uint64_t)std::max<int64_t>(2, 2 * (opt->groups_hint > 0 ? std::min(opt->groups_hint, n) : n));
     while (slots < want) slots <<= 1;
-    int32_t* ht = scr.get_as<int32_t>(slots);
-    int32_t* gid_of_row = scr.get_as<int32_t>(n);
-    int32_t* gidloc = scr.get_as<int32_t>(n);
+    ht = scr.get_as<HEntry<K>>(slots);
     if (scr.failed()) return GJ_ERR_OOM;
-    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
+    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(HEntry<K>) * slots, s))) != GJ_OK) return st;
+    LaunchScope ls(ctx, KK_HGB_GROUP_ID);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)ctx.num_sms * 4));
+    hgb_dict_kernel<K><<<blocks, 512, 0, s>>>((const K*)in->key, n, ht, slots - 1, (unsigned long long*)d_ngroups,
+                                              (K*)out_keys, cap, ctx.d_status);
+  }
+
+  if (variant == GJ_GB_HGB) {
     Aggs A = make_aggs(in, nagg, ops, op_col, out_aggs, in->cols);
-    {
-      LaunchScope ls(ctx, KK_HGB_GROUP_ID);
-      int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx.num_sms * 8);
-      hgb_group_id_kernel<K><<<blocks, 256, 0, s>>>((const K*)in->key, n, ht, slots - 1, gid_of_row, gidloc,
-                                                     (unsigned long long*)d_ngroups, (K*)out_keys, cap,
-                                                     ctx.d_status);
-    }
     {
       LaunchScope ls(ctx, KK_AGG_INIT);
       agg_init_kernel<<<ctx.num_sms * 4, 256, 0, s>>>(A, d_ngroups, cap);
@@ -1194,11 +1159,12 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
         }
       }
     const int budget = ctx.smem_optin - 1024;  // all of an SM's opt-in shared memory for one block
-    if ((st = ensure_smem_attr(ctx, (const void*)hgb_agg_kernel, budget)) != GJ_OK) return st;
+    if ((st = ensure_smem_attr(ctx, (const void*)hgb_aggregate_kernel<K>, budget)) != GJ_OK) return st;
     {
       LaunchScope ls(ctx, KK_HGB_AGG);
-      hgb_agg_kernel<<<ctx.num_sms, 1024, budget, s>>>(gidloc, gid_of_row, n, A, make_col_cache(A), L, d_ngroups,
-                                                       cap, budget);
+      hgb_aggregate_kernel<K><<<ctx.num_sms, 1024, budget, s>>>((const K*)in->key, n, ht, slots - 1, A,
+                                                                 make_col_cache(A), L, d_ngroups, cap, budget,
+                                                                 ctx.d_status);
     }
     return cuda_check(cudaGetLastError());
   }
@@ -1209,24 +1175,14 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   // reduced by the SGB kernels, whose segment i is code i. Reading g to size the
   // sort synchronises the stream once.
   if (variant == GJ_GB_SGB_DE) {
-    uint64_t want = (uint64_t)std::max<int64_t>(2, 2 * (opt->groups_hint > 0 ? std::min(opt->groups_hint, n) : n));
-    uint64_t slots = 1;
-    while (slots < want) slots <<= 1;
-    int32_t* ht = scr.get_as<int32_t>(slots);
-    int32_t* gid_of_row = scr.get_as<int32_t>(n);
-    int32_t* gidloc = scr.get_as<int32_t>(n);
     int32_t* code = scr.get_as<int32_t>(n);
     int32_t* code2 = scr.get_as<int32_t>(n);
     int32_t* code_out = scr.get_as<int32_t>(n);  // the reduction's segment codes (0, 1, ...), unused
     if (scr.failed()) return GJ_ERR_OOM;
-    if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(int32_t) * slots, s))) != GJ_OK) return st;
     {
       LaunchScope ls(ctx, KK_HGB_GROUP_ID);
-      int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx.num_sms * 8);
-      hgb_group_id_kernel<K><<<blocks, 256, 0, s>>>((const K*)in->key, n, ht, slots - 1, gid_of_row, gidloc,
-                                                     (unsigned long long*)d_ngroups, (K*)out_keys, cap,
-                                                     ctx.d_status);
-      de_codes_kernel<<<blocks, 256, 0, s>>>(gidloc, gid_of_row, n, code);
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx.num_sms * 8));
+      hgb_codes_kernel<K><<<blocks, 256, 0, s>>>((const K*)in->key, n, ht, slots - 1, code, ctx.d_status);
     }
     int64_t g = 0;
     if ((st = cuda_check(cudaMemcpyAsync(&g, d_ngroups, sizeof(int64_t), cudaMemcpyDeviceToHost, s))) != GJ_OK)
@@ -1290,16 +1246,66 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   const int kbits = sizeof(K) * 8;
 
   if (variant == GJ_GB_SGB || variant == GJ_GB_SGB_UR) {
-    if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, in->key, k2, cs, n, 0, kbits,
+    // only the key bits that vary are sorted: keys between min and max (in
+    // signed order) share every bit above the highest bit where min and max
+    // differ. Reading the range synchronises the stream once.
+    unsigned long long* d_mm = scr.get_as<unsigned long long>(2);
+    if (scr.failed()) return GJ_ERR_OOM;
+    const unsigned long long init[2] = {~0ull, 0ull};
+    if ((st = cuda_check(cudaMemcpyAsync(d_mm, init, sizeof(init), cudaMemcpyHostToDevice, s))) != GJ_OK) return st;
+    {
+      LaunchScope ls(ctx, KK_RADIX_HIST);
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 4));
+      key_range_kernel<K><<<blocks, 256, 0, s>>>((const K*)in->key, n, d_mm);
+    }
+    unsigned long long mm[2] = {0, 0};
+    if ((st = cuda_check(cudaMemcpyAsync(mm, d_mm, sizeof(mm), cudaMemcpyDeviceToHost, s))) != GJ_OK) return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s))) != GJ_OK) return st;
+    int live = 0;
+    while (live < kbits && ((mm[0] ^ mm[1]) >> live) != 0) ++live;
+    if (live == 0) {
+      // one key value: the input is already sorted
+      Aggs A0 = make_aggs(in, nagg, ops, op_col, out_aggs, in->cols);
+      return sgb_reduce_run<K>(ctx, scr, (const K*)in->key, n, A0, nagg, ops, (K*)out_keys, cap, d_ngroups);
+    }
+    if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, in->key, k2, cs, n, 0, live,
                                   kSignedOrder, opt->bits_per_pass)) != GJ_OK)
       return st;
     return sgb_reduce_run<K>(ctx, scr, k2, n, A, nagg, ops, (K*)out_keys, cap, d_ngroups);
   }
 
-  // PGB-TR / PGB-UR: partitions of about 2048 rows on hashed key bits (at most 16 bits)
+  // shared-memory slot widths as in HGB; the group capacity C of a round is what
+  // fits the block's budget (at most kPgbMaxCap)
+  SmemAggLayout L{};
+  {
+    int q = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < nagg; ++j) {
+        const int w = ops[j] == GJ_AGG_SUM ? 8 : (ops[j] == GJ_AGG_COUNT ? 4 : A.size[j]);
+        if ((pass == 0) == (w == 8)) {
+          L.width[j] = w;
+          L.order[q++] = j;
+          L.bytes_per_group += w;
+        }
+      }
+  }
+  int C = kPgbMaxCap;
+  while (C > 32 && pgb_agg_off<K>(C) + C * L.bytes_per_group > kPgbSmem) C >>= 1;
+  // PGB-TR / PGB-UR: hashed partitions of about 2048 rows (at most 16 bits). With
+  // a groups hint, fewer bits while a partition still holds about C / 2 groups,
+  // but at least 8 (or the row-derived count if smaller), so that every SM gets
+  // several partitions
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : 0;
-  if (opt->radix_bits <= 0)
-    while (bits < 16 && (n >> bits) > 2048) ++bits;
+  if (opt->radix_bits <= 0) {
+    int by_rows = 0;
+    while (by_rows < 16 && (n >> by_rows) > 2048) ++by_rows;
+    bits = by_rows;
+    if (opt->groups_hint > 0) {
+      int by_groups = 0;
+      while (by_groups < 16 && (opt->groups_hint >> by_groups) > C / 2) ++by_groups;
+      bits = std::max(std::min(by_rows, 8), std::min(by_rows, by_groups));
+    }
+  }
   const int64_t nparts = int64_t(1) << bits;
   if (bits > 0) {
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, in->key, k2, cs, n, 0, bits, kHashed,
@@ -1318,27 +1324,14 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     }
   }
   int64_t* poff = scr.get_as<int64_t>(nparts + 1);
-  int64_t* gcount = scr.get_as<int64_t>(nparts + 1);
-  int8_t* qsel = scr.get_as<int8_t>(nparts);
   if (scr.failed()) return GJ_ERR_OOM;
   if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, k2, n, 0, bits, kHashed, poff)) != GJ_OK)
     return st;
-  const size_t dyn = pgb_smem_bytes<K>();
+  const size_t dyn = (size_t)pgb_agg_off<K>(C) + (size_t)C * L.bytes_per_group;
   if ((st = ensure_smem_attr(ctx, (const void*)pgb_kernel<K>, (int)dyn)) != GJ_OK) return st;
-  const ColCache cc = make_col_cache(A);
-  // group counts per partition, their exclusive scan (and g), then the aggregation
-  {
-    LaunchScope ls(ctx, KK_PGB);
-    pgb_kernel<K><<<(unsigned)nparts, kPgbThreads, dyn, s>>>(k2, poff, bits, A, cc, (K*)out_keys, cap, 0, gcount, qsel,
-                                                             ctx.d_status);
-  }
-  {
-    LaunchScope ls(ctx, KK_PGB);
-    excl_scan_kernel<<<1, 1024, 0, s>>>(gcount, nparts, d_ngroups);
-  }
   LaunchScope ls(ctx, KK_PGB);
-  pgb_kernel<K><<<(unsigned)nparts, kPgbThreads, dyn, s>>>(k2, poff, bits, A, cc, (K*)out_keys, cap, 1, gcount, qsel,
-                                                           ctx.d_status);
+  pgb_kernel<K><<<(unsigned)nparts, kPgbThreads, dyn, s>>>(k2, poff, bits, A, make_col_cache(A), L, C, (K*)out_keys,
+                                                           cap, (unsigned long long*)d_ngroups, ctx.d_status);
   return cuda_check(cudaGetLastError());
 }
 

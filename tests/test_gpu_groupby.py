@@ -130,3 +130,26 @@ def test_extreme_int32_values(gj, variant):
     cols = [0, 0, 0, 0]
     got = oracle.canonical(run_gb(gj, key, [v], aggs, cols, variant))
     assert np.array_equal(got, want_rows(key, [v], aggs, cols))
+
+
+@pytest.mark.parametrize("variant", ["hgb", "pgb", "pgb_ur", "sgb_de"])
+@pytest.mark.parametrize("n,g,kdt,theta", [
+    (1 << 20, 16, np.int32, 0.0), (1 << 20, 4096, np.int64, 1.0), (1 << 21, 1 << 16, np.int32, 0.0),
+    (500001, 1 << 12, np.int32, 1.2), (77777, 3, np.int64, 0.0)])
+def test_groupby_with_groups_hint(gj, variant, n, g, kdt, theta):
+    # the hint sizes HGB's dictionary and sets PGB's partition bits (few, large
+    # partitions for few groups): results are unchanged
+    w = wl.groupby_workload(n, g, nvals=3, key_dtype=kdt, theta=theta, seed=n ^ g)
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], AGGS, COLS, variant, groups_hint=g))
+    assert np.array_equal(got, want_rows(w["key"], w["vals"], AGGS, COLS))
+
+
+@pytest.mark.parametrize("variant", ["hgb", "pgb"])
+def test_one_hot_key_per_warp(gj, variant):
+    # every row has the same key: each warp's 32 rows are combined before one atomic
+    n = 300001
+    key = np.full(n, -7, dtype=np.int32)
+    rng = np.random.default_rng(4)
+    vals = [rng.integers(-(2**31), 2**31, n, dtype=np.int64).astype(np.int32) for _ in range(3)]
+    got = run_gb(gj, key, vals, AGGS, COLS, variant, groups_hint=1)
+    assert np.array_equal(oracle.canonical(got), want_rows(key, vals, AGGS, COLS))
