@@ -146,33 +146,109 @@ def oracle_sample(fn, rows: int, what: str):
             "sample": f"{what}, {dt:.1f} s"}
 
 
-def bench_groupby(gj, wl, peak, steps: int = 5, log2_groups: int = 20, cpu: bool = True):
-    """Plain grouped aggregation: 2^27 rows, int32 keys from 2^log2_groups ids,
-    3 int32 value columns, COUNT + SUM/MIN/MAX per column (10 int64 aggregates)."""
+GB_VARIANTS = ("hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de")
+
+
+def groupby_alg_bytes(kind: str, variant: str, n: int, k: int, d: int, launches: int) -> float:
+    """Algorithmic bytes one call moves in the kernels of `kind` (n rows, k-byte
+    keys, three 4-byte value columns, d groups of 10 int64 aggregates):
+    radix passes read and write key + what travels with it (values for TR, a
+    4-byte tuple id for UR, 4-byte codes + values for SGB-DE); histograms and
+    bounds read the key; a group-id, aggregation or reduction pass reads key and
+    values and writes each group once."""
+    vals, out = 12, k + 80
+    moved = {"sgb": k + vals, "pgb": k + vals, "sgb_ur": k + 4, "pgb_ur": k + 4, "sgb_de": 4 + vals}.get(variant, k)
+    if kind == "radix_scatter":
+        return launches * 2.0 * n * moved
+    if kind == "radix_hist":   # key range (SGB), tile histograms (per pass); the offset scans are not counted
+        return launches / 2.0 * n * (4 if variant == "sgb_de" else k)
+    if kind == "partition_bounds":
+        return n * k
+    if kind == "hgb_group_id":  # dictionary pass (+ the code pass of SGB-DE)
+        return n * k * (2 if variant == "sgb_de" else 1) + (4 * n if variant == "sgb_de" else 0)
+    if kind in ("hgb_aggregate", "pgb", "sgb_reduce"):
+        key = 4 if variant == "sgb_de" else k
+        return n * (key + vals) + d * out + (n * key if kind == "sgb_reduce" else 0)
+    if kind == "agg_init":
+        return d * 80
+    return 0.0
+
+
+def bench_groupby(gj, wl, peak, steps: int = 5, cpu: bool = True):
+    """Plain grouped aggregation over every cell of the workload: n = 2^27 rows,
+    int32 or int64 keys over 2^4, 2^12, 2^20 or 2^26 ids, uniform or Zipf 1.0, three
+    int32 value columns in [-2^20, 2^20), COUNT + SUM/MIN/MAX per column (10 int64
+    aggregates); every variant, with the cell's cardinality as the groups hint."""
     import torch
-    n, g = 1 << 27, 1 << log2_groups
-    w = wl.groupby_workload(n, g, nvals=3, seed=77)
-    key = torch.from_numpy(w["key"]).cuda()
-    vals = [torch.from_numpy(v).cuda() for v in w["vals"]]
+    n = 1 << 27
     aggs = ["count"] + ["sum", "min", "max"] * 3
     cols = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
-    distinct = int(np.unique(w["key"]).size)
-    min_bytes = n * (4 + 12) + distinct * (4 + 80)
-    out = {"workload": f"n=2^27 int32 keys over 2^{log2_groups} ids ({distinct} groups), 3 int32 values, "
-                       f"COUNT+SUM/MIN/MAX per column", "min_bytes": min_bytes}
-    for v in ("hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"):
-        okeys, outs, ng = gj.groupby(key, vals, aggs, cols, variant=v, sync=True)
-        assert int(ng.item()) == distinct
-        ms = _event_ms(lambda: gj.groupby(key, vals, aggs, cols, variant=v, sync=False), steps)
-        out[v] = {"ms": ms, "gtuples_s": n / (ms * 1e-3) / 1e9,
-                  "min_bytes_frac": min_bytes / (ms * 1e-3) / 1e9 / peak}
-    del key, vals
+    cells = []
+    for lg in (4, 12, 20, 26):
+        for kdt in (np.int32, np.int64):
+            for theta in (0.0, 1.0):
+                w = wl.groupby_workload(n, 1 << lg, nvals=3, key_dtype=kdt, theta=theta, seed=77)
+                k = np.dtype(kdt).itemsize
+                key = torch.from_numpy(w["key"]).cuda()
+                vals = [torch.from_numpy(v).cuda() for v in w["vals"]]
+                distinct = int(torch.unique(key).numel())
+                min_bytes = n * (k + 12) + distinct * (k + 80)
+                cell = {"ids": f"2^{lg}", "key_bytes": k, "zipf": theta, "groups": distinct, "min_bytes": min_bytes}
+                for v in GB_VARIANTS:
+                    call = lambda: gj.groupby(key, vals, aggs, cols, variant=v, sync=False, groups_hint=1 << lg)
+                    _, _, ng = gj.groupby(key, vals, aggs, cols, variant=v, sync=True, groups_hint=1 << lg)
+                    assert int(ng.item()) == distinct
+                    ms = _event_ms(call, steps)
+                    gj.profile_read()
+                    gj.profile_enable(True)
+                    call()
+                    prof = gj.profile_read()
+                    gj.profile_enable(False)
+                    dom = max(prof, key=lambda q: prof[q][0])
+                    dms, dl = prof[dom]
+                    ab = groupby_alg_bytes(dom, v, n, k, distinct, dl)
+                    ach = ab / (dms * 1e-3) / 1e9
+                    cell[v] = {"ms": ms, "gtuples_s": n / (ms * 1e-3) / 1e9,
+                               "min_bytes_frac": min_bytes / (ms * 1e-3) / 1e9 / peak,
+                               "roofline": {"bound": "hbm", "kernel": dom, "launches": dl, "achieved": ach,
+                                            "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                                            "alg_bytes_per_launch": ab / dl},
+                               "kernels_ms": {q: round(t, 4) for q, (t, c) in prof.items()}}
+                cells.append(cell)
+                del key, vals
+    out = {"workload": "n=2^27, keys int32/int64 over 2^4/2^12/2^20/2^26 ids, uniform or Zipf 1.0, 3 int32 values, "
+                       "COUNT+SUM/MIN/MAX per column (10 int64 aggregates), groups hint = ids",
+           "cells": cells}
     if cpu:
-        m = 1 << 24  # the first 2^24 rows of the same input
+        m = 1 << 24  # the first 2^24 rows of the 2^20-id uniform int32 input
+        w = wl.groupby_workload(n, 1 << 20, nvals=3, seed=77)
         out["cpu_baseline"] = oracle_sample(
             lambda o: o.groupby_hash(w["key"][:m], [c[:m] for c in w["vals"]], aggs, cols), m,
-            "first 2^24 rows of the same input, std::unordered_map group-by, 10 aggregates")
+            "first 2^24 rows of the 2^20-id uniform int32 input, std::unordered_map group-by, 10 aggregates")
     return out
+
+
+def bench_gather(gj, steps: int = 10):
+    """The paper's gather calibration (Sec. 4.1.1, Table gather-profile) on this
+    GPU: gather 2^27 4-byte elements through a clustered map (the identity) and
+    an unclustered one (a seeded random permutation). Both read the map and write
+    the output sequentially (8 bytes per element at B_G); the input costs 4 bytes
+    at B_G when clustered and at B_R when not, so with r = t_unclustered /
+    t_clustered, B_G / B_R = 3 r - 2 (the paper's A100 figure: r = 8.52, 24)."""
+    import torch
+    n = 1 << 27
+    src = torch.randint(-(2**31), 2**31 - 1, (n,), dtype=torch.int32, device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(3))
+    ident = torch.arange(n, dtype=torch.int32, device="cuda")
+    perm = torch.randperm(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4)).to(torch.int32)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    tc = _event_ms(lambda: gj.gather(src, ident, sync=False, out=out), steps)
+    tu = _event_ms(lambda: gj.gather(src, perm, sync=False, out=out), steps)
+    assert gj.device_status() == 0
+    r = tu / tc
+    return {"workload": "gather of 2^27 int32 elements, identity vs random permutation map",
+            "clustered_ms": tc, "unclustered_ms": tu, "ratio": r, "bg_over_br": 3 * r - 2,
+            "clustered_gb_s": 12 * n / (tc * 1e-3) / 1e9}
 
 
 def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 6784.5):
@@ -443,15 +519,20 @@ def main():
         step()
     prof = gj.profile_read()
     gj.profile_enable(False)
+    # partition passes per side, from the scatter launches (one per pass and side)
+    passes = prof.get("radix_scatter", (0.0, 2 * args.steps))[1] / (2 * args.steps)
     alg_bytes_per_step = {
-        # two passes (8 + 7 bits) over R and over S, each reading and writing key + payloads
-        "radix_scatter": 2 * 2 * (NR + NS) * ROW_BYTES,
+        # every pass over R and over S reads and writes key + payloads
+        "radix_scatter": passes * 2 * (NR + NS) * ROW_BYTES,
         # per pass, one read of every key for the tile histograms (the per-digit
         # scans of the tile counts are not counted)
-        "radix_hist": 2 * 4 * (NR + NS),
+        "radix_hist": passes * 4 * (NR + NS),
         # read S' and R' once, write T
         "phj_probe": (NR + NS) * ROW_BYTES + NS * OUT_ROW_BYTES,
         "partition_bounds": 4 * NR,
+        # L2-sized partitions: clear and fill the tables (about 2-4 slots of 4 bytes
+        # per build row; counted as 2), reading the build keys
+        "nphj_build": 4 * NR + 2 * 2 * 4 * NR,
     }
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
@@ -556,6 +637,7 @@ def main():
             out["one_query"] = bench_one_query(gj, wl, cpu=cpu, peak=peak)
             out["batched"] = bench_batch(gj, wl, cpu=cpu, peak=peak)
             out["many_to_many"] = bench_many_to_many(gj, wl, peak=peak)
+            out["gather_calibration"] = bench_gather(gj)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -178,6 +178,15 @@ gj_status gj_radix_partition(const gj_table* in, int32_t bit_lo, int32_t bit_hi,
 gj_status gj_radix_partition_noalloc(const gj_table* in, int32_t bit_lo, int32_t bit_hi, int32_t key_transform,
                                      gj_table* out, int64_t* d_offsets, int32_t sync, void* stream);
 
+/* gather (Sec. 2.3): out[i] = in[map[i]] for i < n; in holds n_in elements of
+ * elem_bytes (4 or 8) bytes, map n int32 indices, out n elements (all device
+ * memory, not overlapping). A clustered map (indices in order, or nearly) reads
+ * in sequentially; an unclustered one (a random permutation) reads it at
+ * random. An index outside [0, n_in) is recorded as GJ_ERR_INVALID_ARG on the
+ * device (returned with opt->sync = 1) and its out[i] is left unwritten. */
+gj_status gj_gather(const void* in, int64_t n_in, int32_t elem_bytes, const int32_t* map, int64_t n, void* out,
+                    const gj_options* opt, void* stream);
+
 /* Inner equi-join (Sec. 2.2): T(key, R.cols.., S.cols..) = { (r.key, r.., s..) :
  * r in R, s in S, r.key = s.key }. For the primary-key variants (PHJ_TR, PHJ_UR,
  * NPHJ, SMJ_TR, SMJ_UR and AUTO) R.key must be unique; a repeated key yields
@@ -279,21 +288,22 @@ gj_status gj_batch_get_config(const gj_batch_plan* plan, gj_batch_config* cfg);
 gj_status gj_batch_destroy(gj_batch_plan* plan);
 
 /* ---- Learned variant selector ---------------------------------------------
- * A multi-layer perceptron x(12) -> 64 -> ReLU -> 64 -> ReLU -> y(6), FP32,
- * predicting log run time of the join variants PHJ-TR, PHJ-UR, NPHJ (y0..y2)
- * and the group-by variants HGB, SGB, PGB (y3..y5). The paper chooses variants
- * with cost models and heuristics (Sec. 4.1.3, 4.1.4, 4.4, 5.1.10, Fig.
- * groupby-dt); the network has no counterpart there and those rules remain the
- * fallback. Parameters are one float array of GJ_MLP_PARAMS values, row-major
- * [out][in] weights each followed by its bias: w1[64][12] b1[64] w2[64][64]
- * b2[64] w3[6][64] b3[6]. All pointers below are device memory; all calls are
- * asynchronous on `stream`. */
+ * A multi-layer perceptron x(12) -> 64 -> ReLU -> 64 -> ReLU -> y(11), FP32,
+ * predicting log run time of the join variants PHJ-TR, PHJ-UR, NPHJ, SMJ-TR,
+ * SMJ-UR (y0..y4) and the group-by variants HGB, SGB, PGB, SGB-UR, PGB-UR,
+ * SGB-DE (y5..y10). The paper chooses variants with cost models and heuristics
+ * (Sec. 4.1.3, 4.1.4, 4.4, 5.1.10, Fig. groupby-dt); the network has no
+ * counterpart there and those rules remain the fallback. Parameters are one
+ * float array of GJ_MLP_PARAMS values, row-major [out][in] weights each followed
+ * by its bias: w1[64][12] b1[64] w2[64][64] b2[64] w3[11][64] b3[11]. All
+ * pointers below are device memory; all calls are asynchronous on `stream`. */
 #define GJ_MLP_IN 12
 #define GJ_MLP_HIDDEN 64
-#define GJ_MLP_OUT 6
-#define GJ_MLP_PARAMS 5382
+#define GJ_MLP_OUT 11
+#define GJ_MLP_JOIN_OUT 5
+#define GJ_MLP_PARAMS 5707
 
-/* y[batch][6] = f(theta, x[batch][12]). */
+/* y[batch][11] = f(theta, x[batch][12]). */
 gj_status gj_mlp_forward(const float* theta, const float* x, int32_t batch, float* y, void* stream);
 /* loss = (1/batch) sum_b sum_o mask[b][o] (y[b][o] - t[b][o])^2 and its gradient
  * grad[GJ_MLP_PARAMS] (overwritten). Reductions run in a fixed order, so the
@@ -306,13 +316,15 @@ gj_status gj_mlp_adam_step(float* theta, const float* grad, float* m, float* v, 
                            float beta2, float eps, void* stream);
 /* theta -= lr * grad. */
 gj_status gj_mlp_sgd_step(float* theta, const float* grad, float lr, void* stream);
-/* For each of n feature rows (already normalised), the argmin of y0..y2 as a
- * gj_join_variant (1 + index) and of y3..y5 as a gj_groupby_variant. */
+/* For each of n feature rows (already normalised), the argmin of y0..y4 as a
+ * gj_join_variant (PHJ_TR, PHJ_UR, NPHJ, SMJ_TR, SMJ_UR) and of y5..y10 as a
+ * gj_groupby_variant (1 + index - 5). */
 gj_status gj_mlp_select(const float* theta, const float* x, int32_t n, int32_t* join_variant, int32_t* gb_variant,
                         void* stream);
 
-/* Selector used by gj_join / gj_groupby when a variant is AUTO and
- * options.selector = GJ_SELECT_MLP. host_theta: GJ_MLP_PARAMS floats (host);
+/* Selector used by gj_join / gj_groupby / gj_join_groupby when a variant is
+ * AUTO and options.selector = GJ_SELECT_MLP (gj_join_groupby, which runs
+ * PHJ-TR, PHJ-UR and NPHJ only, takes the argmin of y0..y2). host_theta: GJ_MLP_PARAMS floats (host);
  * mean / stdev: GJ_MLP_IN floats (host) normalising the raw features
  * (x - mean) / stdev. Passing NULL theta removes the network, and AUTO falls
  * back to the paper's rules. The raw features of a query are

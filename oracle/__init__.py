@@ -147,6 +147,12 @@ def radix_partition(key, key_bytes: int, lo: int, hi: int, transform: int = 0):
     return perm, offs
 
 
+def gather(src, index) -> np.ndarray:
+    """The gather primitive (Sec. 2.3): out[i] = src[index[i]]."""
+    src = np.asarray(src)
+    return np.array([src[int(j)] for j in np.asarray(index)], dtype=src.dtype)
+
+
 def canonical(rows: np.ndarray) -> np.ndarray:
     """Rows sorted lexicographically by all columns (signed int64): the comparison form."""
     rows = np.asarray(rows, dtype=np.int64)

@@ -1,7 +1,7 @@
 """float64 reference of the variant-selector MLP -- TEST INFRASTRUCTURE ONLY.
 
 Network: x (12 features) -> Linear(12, 64) -> ReLU -> Linear(64, 64) -> ReLU ->
-Linear(64, 6); loss = (1 / batch) * sum over samples and outputs of
+Linear(64, 11); loss = (1 / batch) * sum over samples and outputs of
 mask * (y - t)^2 (outputs without a target have mask 0). Weights are row-major
 [out][in]. This is the plain
 textbook definition of a two-hidden-layer perceptron with a masked squared
@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import numpy as np
 
-D_IN, D_H, D_OUT = 12, 64, 6
+D_IN, D_H, D_OUT = 12, 64, 11
 SHAPES = [("w1", (D_H, D_IN)), ("b1", (D_H,)), ("w2", (D_H, D_H)), ("b2", (D_H,)),
           ("w3", (D_OUT, D_H)), ("b3", (D_OUT,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)

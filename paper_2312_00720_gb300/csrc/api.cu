@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -66,7 +67,7 @@ cudaEvent_t take_event() {
 const char* const kKindNames[KK_COUNT] = {
     "radix_hist", "radix_scatter", "partition_bounds", "phj_probe", "nphj_build", "nphj_probe",
     "hgb_group_id", "hgb_aggregate", "pgb", "sgb_reduce", "agg_init", "fused_probe", "group_emit",
-    "batch", "mlp", "smj_merge"};
+    "batch", "mlp", "smj_merge", "gather"};
 
 }  // namespace
 
@@ -183,6 +184,38 @@ __global__ void wait_check_kernel(int kind, uint64_t* words, int* status) {
     if (threadIdx.x == 0) mbar_wait(&s_bar, 0, status);  // no arrival, no copy in flight
   } else {
     block_wait((const unsigned long long*)words + 1, 1ull, status);  // word 1 stays 0
+  }
+}
+
+// out[i] = in[map[i]] (the gather primitive): map read and out written in order,
+// in read wherever map points. An index outside [0, n_in) records
+// GJ_ERR_INVALID_ARG and leaves out[i] as it was.
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(const T* __restrict__ in, int64_t n_in,
+                                                     const int32_t* __restrict__ map, int64_t n, T* __restrict__ out,
+                                                     int* status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  constexpr int kBatch = 4;  // loads of the batch in flight together
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kBatch) {
+    int32_t m[kBatch];
+    T v[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) m[u] = i0 + u * stride < n ? __ldcs(map + i0 + u * stride) : 0;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const bool ok = i0 + u * stride < n && m[u] >= 0 && m[u] < n_in;
+      v[u] = ok ? in[m[u]] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n) continue;
+      if (m[u] < 0 || m[u] >= n_in) {
+        set_status(status, GJ_ERR_INVALID_ARG);
+        continue;
+      }
+      __stcs(out + i, v[u]);
+    }
   }
 }
 
@@ -405,6 +438,28 @@ gj_status gj_auto_variants(const gj_table* R, const gj_table* S, int32_t nagg, c
     *gb_variant = resolve_groupby_variant(S, nagg, ops, opt, std::min(smem, 200 * 1024) - 1024);
   }
   return GJ_OK;
+}
+
+gj_status gj_gather(const void* in, int64_t n_in, int32_t elem_bytes, const int32_t* map, int64_t n, void* out,
+                    const gj_options* opt, void* stream) {
+  if (n < 0 || n_in < 0 || (elem_bytes != 4 && elem_bytes != 8)) return GJ_ERR_INVALID_ARG;
+  if (n > 0 && (!in || !map || !out)) return GJ_ERR_INVALID_ARG;
+  if (n > kMaxRows || n_in > kMaxRows) return GJ_ERR_UNSUPPORTED;
+  Ctx ctx;
+  gj_status st = make_ctx(stream, &ctx);
+  if (st != GJ_OK) return st;
+  if (n > 0) {
+    LaunchScope ls(ctx, KK_GATHER);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 8));
+    if (elem_bytes == 4)
+      gather_kernel<int32_t><<<blocks, 256, 0, ctx.stream>>>((const int32_t*)in, n_in, map, n, (int32_t*)out,
+                                                             ctx.d_status);
+    else
+      gather_kernel<int64_t><<<blocks, 256, 0, ctx.stream>>>((const int64_t*)in, n_in, map, n, (int64_t*)out,
+                                                             ctx.d_status);
+    st = cuda_check(cudaGetLastError());
+  }
+  return finish(ctx, opt, st);
 }
 
 gj_status gj_set_wait_limit(uint64_t ns) {

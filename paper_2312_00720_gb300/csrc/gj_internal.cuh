@@ -411,6 +411,7 @@ enum KernelKind {
   KK_BATCH,
   KK_MLP,
   KK_SMJ_MERGE,
+  KK_GATHER,
   KK_COUNT
 };
 // Brackets one kernel launch: counts it and, when timing is on, records CUDA

@@ -106,7 +106,7 @@ __device__ __forceinline__ int32_t hgb_find(const HEntry<K>* __restrict__ ht, ui
 // so that a key repeated across the block's rows reaches the global table once per
 // block. 4-byte keys are tagged with bit 32 (empty = 0); 8-byte keys are stored as
 // they are (empty = INT64_MIN, a key of that value is simply never cached).
-constexpr int kSeenSlots = 4096;
+constexpr int kSeenSlots = 16384;  // 128 KB: one 1024-thread block per SM
 constexpr int kSeenProbes = 4;
 template <typename K>
 __device__ __forceinline__ unsigned long long seen_tag(K k) {
@@ -119,12 +119,16 @@ __device__ __forceinline__ unsigned long long seen_empty() {
 
 // Stage 1: build the dictionary. Writes nothing per row.
 template <typename K>
-__global__ void __launch_bounds__(512) hgb_dict_kernel(const K* __restrict__ key, int64_t n, HEntry<K>* ht,
+__global__ void __launch_bounds__(1024, 1) hgb_dict_kernel(const K* __restrict__ key, int64_t n, HEntry<K>* ht,
                                                        uint64_t mask, unsigned long long* ngroups,
-                                                       K* __restrict__ out_keys, int64_t cap, int* err) {
-  __shared__ unsigned long long s_seen[kSeenSlots];
+                                                       K* __restrict__ out_keys, int64_t cap, const int* gate,
+                                                       int* err) {
+  if (gate && *gate == 0) return;  // the few-groups pass has produced the result
+  extern __shared__ unsigned long long s_seen[];  // kSeenSlots entries
+  __shared__ int s_fill;  // keys cached; new keys stop being cached at half load
   const unsigned long long empty = seen_empty<K>();
   for (int j = threadIdx.x; j < kSeenSlots; j += blockDim.x) s_seen[j] = empty;
+  if (threadIdx.x == 0) s_fill = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   constexpr int kBatch = 4;  // rows per thread per step: their key loads are in flight together
@@ -146,8 +150,12 @@ __global__ void __launch_bounds__(512) hgb_dict_kernel(const K* __restrict__ key
         for (int p = 0; p < kSeenProbes; ++p) {
           unsigned long long v = s_seen[s];
           if (v == empty) {
+            if (*(volatile int*)&s_fill >= kSeenSlots / 2) break;  // full enough: look up only
             v = atomicCAS(&s_seen[s], empty, tag);
-            if (v == empty) break;  // this row inserts the key on the block's behalf
+            if (v == empty) {
+              atomicAdd(&s_fill, 1);
+              break;  // this row inserts the key on the block's behalf
+            }
           }
           if (v == tag) {
             handled = true;  // another row of the block has inserted or found it
@@ -179,7 +187,8 @@ __global__ void hgb_codes_kernel(const K* __restrict__ key, int64_t n, const HEn
 // 32 bits, so the result is unchanged, and a block's shared-memory slot still at
 // that identity has nothing to add (it may hold a real INT32_MAX, which then is
 // already the starting value).
-__global__ void agg_init_kernel(Aggs A, const int64_t* __restrict__ ngroups, int64_t cap) {
+__global__ void agg_init_kernel(Aggs A, const int64_t* __restrict__ ngroups, int64_t cap, const int* gate) {
+  if (gate && *gate == 0) return;
   const int64_t g = min64(*ngroups, cap);
   const int64_t total = g * A.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -202,25 +211,7 @@ struct SmemAggLayout {
   int32_t bytes_per_group;
 };
 
-// Adds v (for COUNT: a count of rows) into one shared-memory slot.
-__device__ __forceinline__ void smem_update(int op, int width, unsigned char* slot, int64_t v) {
-  if (width == 8) {
-    agg_atomic(op, (int64_t*)slot, v);
-  } else if (op == GJ_AGG_COUNT) {
-    atomicAdd((unsigned int*)slot, (unsigned int)v);
-  } else if (op == GJ_AGG_MIN) {
-    atomicMin((int*)slot, (int)v);
-  } else {
-    atomicMax((int*)slot, (int)v);
-  }
-}
-
-__device__ __forceinline__ int64_t smem_read(int op, int width, const unsigned char* slot) {
-  if (width == 8) return *(const int64_t*)slot;
-  if (op == GJ_AGG_COUNT) return (int64_t) * (const unsigned int*)slot;
-  return (int64_t) * (const int*)slot;
-}
-
+// Starting value of a slot (zero for both SUM forms).
 __device__ __forceinline__ void smem_init(int op, int width, unsigned char* slot) {
   if (width == 8)
     *(int64_t*)slot = agg_identity(op);
@@ -230,49 +221,94 @@ __device__ __forceinline__ void smem_init(int op, int width, unsigned char* slot
     *(int*)slot = op == GJ_AGG_MIN ? INT32_MAX : INT32_MIN;
 }
 
-// One warp-wide step of an aggregation: every lane holds one row (ok = it takes
-// part, gid its group, cv its cached 4-byte values at position u). Lanes of equal
-// gid are combined first (match.any, then redux.sync: COUNT is the peer count,
-// SUM adds the high and low 16-bit halves separately so 32 values never overflow,
-// MIN/MAX directly) and only the lowest lane of each group calls update(j, gid, v);
-// when the step holds no repeated group every lane updates for itself. Aggregates
-// over columns outside the cache are never combined.
-template <int B, typename Update>
-__device__ __forceinline__ void warp_aggregate(const Aggs& A, const ColCache& cc, bool ok, int32_t gid,
-                                               const int32_t (&cv)[kColCache][B], int u, int64_t row,
-                                               Update&& update) {
-  const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(0xffffffffu, ok ? gid : -1 - lane);
-  if (!__any_sync(0xffffffffu, __popc(peers) > 1)) {
-    if (ok)
-      for (int j = 0; j < A.n; ++j) update(j, gid, cached_value<B>(A, cc, j, cv, u, row));
-    return;
+// Slot forms of an aggregate in shared memory: 32-bit (COUNT; MIN/MAX over a
+// 4-byte column), int64, or a SUM split over two 32-bit words that add the
+// value's low 16 bits (unsigned) and high 16 bits (signed) separately.
+// Shared-memory 64-bit additions run as compare-and-swap loops that collapse
+// when many lanes hit one slot, while 32-bit atomics are resolved in hardware;
+// the split form is exact while a slot takes at most kSplitRows values (its
+// words stay below 2^32 and 2^31), after which it is folded away.
+enum SlotForm { kSlot32 = 0, kSlot64 = 1, kSlotSplit = 2 };
+
+// One aggregate with its operation, value source (a cached 4-byte column 0..2, or
+// -1: COUNT, or a column read through Aggs) and slot form fixed at compile time,
+// so the per-row update is a handful of instructions.
+template <int OP, int SRC, int FORM>
+struct SlotUpd {
+  static constexpr int kWidth = FORM == kSlot32 ? 4 : 8;
+  template <int B>
+  static __device__ __forceinline__ int64_t value(const Aggs& A, int j, const int32_t (&cv)[kColCache][B], int u,
+                                                  int64_t row) {
+    if (OP == GJ_AGG_COUNT) return 1;
+    if (SRC >= 0) return cv[SRC][u];
+    return load_as_i64(A.src[j], A.size[j], A.tid ? (int64_t)A.tid[row] : row);
   }
-  const bool leader = ok && lane == __ffs(peers) - 1;
-  for (int j = 0; j < A.n; ++j) {
-    const int op = A.op[j];
-    const int s = cc.slot[j];
-    int64_t v;
-    if (op == GJ_AGG_COUNT) {
-      v = __popc(peers);
-    } else if (s >= 0) {
-      const int32_t x = s == 0 ? cv[0][u] : (s == 1 ? cv[1][u] : cv[2][u]);
-      if (op == GJ_AGG_SUM) {
-        const int hi = __reduce_add_sync(peers, x >> 16);
-        const unsigned lo = __reduce_add_sync(peers, (unsigned)(x & 0xffff));
-        v = (int64_t)hi * 65536 + (int64_t)lo;
-      } else if (op == GJ_AGG_MIN) {
-        v = __reduce_min_sync(peers, x);
-      } else {
-        v = __reduce_max_sync(peers, x);
-      }
+  static __device__ __forceinline__ void apply(unsigned char* slot, int64_t v) {
+    if (FORM == kSlotSplit) {
+      atomicAdd((unsigned int*)slot, (unsigned int)(v & 0xffff));
+      atomicAdd((int*)slot + 1, (int)(v >> 16));
+    } else if (FORM == kSlot64) {
+      agg_atomic(OP, (int64_t*)slot, v);
+    } else if (OP == GJ_AGG_COUNT) {
+      atomicAdd((unsigned int*)slot, 1u);
+    } else if (OP == GJ_AGG_MIN) {
+      atomicMin((int*)slot, (int)v);
     } else {
-      if (ok) update(j, gid, cached_value<B>(A, cc, j, cv, u, row));
-      continue;
+      atomicMax((int*)slot, (int)v);
     }
-    if (leader) update(j, gid, v);
   }
+};
+
+__host__ __device__ __forceinline__ int slot_code(int op, int src, int form) { return op * 16 + (src + 1) * 4 + form; }
+
+// The form and dispatch code of aggregate j: split SUMs need a cached 4-byte column.
+__device__ __forceinline__ int slot_form(const Aggs& A, const ColCache& cc, int j, bool split) {
+  const int op = A.op[j];
+  if (op == GJ_AGG_COUNT) return kSlot32;
+  if (op == GJ_AGG_SUM) return split && cc.slot[j] >= 0 ? kSlotSplit : kSlot64;
+  return A.size[j] == 4 ? kSlot32 : kSlot64;
 }
+
+// Calls f(SlotUpd<...>{}) for a code made by slot_code (a switch over the 18
+// combinations that occur).
+template <typename F>
+__device__ __forceinline__ void slot_dispatch(int code, F&& f) {
+#define GJ_UPD_CASE(OP, SRC, FORM) \
+  case (OP) * 16 + ((SRC) + 1) * 4 + (FORM): f(SlotUpd<OP, SRC, FORM>{}); return;
+  switch (code) {
+    GJ_UPD_CASE(GJ_AGG_COUNT, -1, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_SUM, 0, kSlot64)
+    GJ_UPD_CASE(GJ_AGG_SUM, 1, kSlot64)
+    GJ_UPD_CASE(GJ_AGG_SUM, 2, kSlot64)
+    GJ_UPD_CASE(GJ_AGG_SUM, -1, kSlot64)
+    GJ_UPD_CASE(GJ_AGG_SUM, 0, kSlotSplit)
+    GJ_UPD_CASE(GJ_AGG_SUM, 1, kSlotSplit)
+    GJ_UPD_CASE(GJ_AGG_SUM, 2, kSlotSplit)
+    GJ_UPD_CASE(GJ_AGG_MIN, 0, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MIN, 1, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MIN, 2, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MIN, -1, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MIN, -1, kSlot64)
+    GJ_UPD_CASE(GJ_AGG_MAX, 0, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MAX, 1, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MAX, 2, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MAX, -1, kSlot32)
+    GJ_UPD_CASE(GJ_AGG_MAX, -1, kSlot64)
+    default: return;
+  }
+#undef GJ_UPD_CASE
+}
+
+// Value of a slot of the given form.
+__device__ __forceinline__ int64_t slot_read(int op, int form, const unsigned char* p) {
+  if (form == kSlotSplit) return (int64_t)(*((const int*)p + 1)) * 65536 + (int64_t)(*(const unsigned int*)p);
+  if (form == kSlot64) return *(const int64_t*)p;
+  if (op == GJ_AGG_COUNT) return (int64_t) * (const unsigned int*)p;
+  return (int64_t) * (const int*)p;
+}
+
+// Rows a split SUM slot may take before its 32-bit words are folded away.
+constexpr int64_t kSplitRows = 65535;
 
 // Stage 2: every row's group id from the dictionary, then its aggregates. When
 // the g groups' slots fit in shared memory (is_smem_enough, decided here on the
@@ -285,8 +321,11 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
                                                                 const HEntry<K>* __restrict__ ht, uint64_t mask,
                                                                 Aggs A, ColCache cc, SmemAggLayout L,
                                                                 const int64_t* __restrict__ ngroups, int64_t cap,
-                                                                int smem_budget, int* err) {
+                                                                int smem_budget, const int* gate, int* err) {
+  if (gate && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char s_agg[];
+  __shared__ int64_t offs[kMaxAggs];  // aggregate j's slot array within a copy
+  __shared__ int s_code[kMaxAggs];
   const int64_t g = min64(*ngroups, cap);
   const int64_t copy_bytes = (g * (int64_t)L.bytes_per_group + 15) & ~int64_t(15);
   const bool use_smem = copy_bytes <= smem_budget;  // is_smem_enough
@@ -294,7 +333,11 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
   int ncopy = 1;
   while (use_smem && ncopy < nwarps && 2 * ncopy * copy_bytes <= smem_budget) ncopy *= 2;
   const int warp = threadIdx.x >> 5;
-  __shared__ int64_t offs[kMaxAggs];  // aggregate j's slot array within a copy
+  // split SUMs (32-bit atomics only) for up to 1024 groups, folded into the result
+  // every epoch: a copy takes at most (nwarps / ncopy) * 32 * kBatch rows per step
+  constexpr int kBatch = 4;  // rows per thread per step: loads and lookups of the batch overlap
+  const bool split = use_smem && g <= 1024;
+  const int epoch_steps = (int)(kSplitRows / ((nwarps / ncopy) * 32 * kBatch));
   if (threadIdx.x == 0) {
     int64_t o = 0;
     for (int q = 0; q < A.n; ++q) {
@@ -302,6 +345,10 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
       offs[j] = o;
       o += g * L.width[j];
     }
+  }
+  if (threadIdx.x < A.n) {
+    const int j = threadIdx.x;
+    s_code[j] = slot_code(A.op[j], A.op[j] == GJ_AGG_COUNT ? -1 : cc.slot[j], slot_form(A, cc, j, split));
   }
   __syncthreads();
   if (use_smem) {
@@ -313,10 +360,26 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
       }
     __syncthreads();
   }
+  // adds the split SUM words of every copy into the result and clears them
+  auto fold_split = [&]() {
+    for (int j = 0; j < A.n; ++j) {
+      if ((s_code[j] & 3) != kSlotSplit) continue;
+      for (int64_t s = threadIdx.x; s < g; s += blockDim.x) {
+        int64_t v = 0;
+        for (int c = 0; c < ncopy; ++c) {
+          unsigned char* p = s_agg + c * copy_bytes + offs[j] + s * 8;
+          v += slot_read(GJ_AGG_SUM, kSlotSplit, p);
+          *(int64_t*)p = 0;
+        }
+        if (v != 0) agg_atomic(GJ_AGG_SUM, &A.out[j][s], v);
+      }
+    }
+  };
   unsigned char* mine = s_agg + (warp & (ncopy - 1)) * copy_bytes;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int kBatch = 4;  // rows per thread per step: loads and lookups of the batch overlap
   bool lost = false;
+  int step = 0;
+  // the loop bound is the block's first row: every thread runs the same steps
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it - threadIdx.x < n; it += stride * kBatch) {
     int64_t row[kBatch];
     bool valid[kBatch];
@@ -332,34 +395,285 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
     for (int u = 0; u < kBatch; ++u) gid[u] = valid[u] ? hgb_find<K>(ht, mask, kk[u]) : -1;
     int32_t cv[kColCache][kBatch];
     load_cached<kBatch>(cc, row, valid, cv);
+    bool ok[kBatch];
 #pragma unroll
     for (int u = 0; u < kBatch; ++u) {
       lost |= valid[u] && gid[u] < 0;
-      const bool ok = valid[u] && gid[u] >= 0 && gid[u] < g;
-      if (use_smem)
-        warp_aggregate<kBatch>(A, cc, ok, gid[u], cv, u, row[u], [&](int j, int32_t gr, int64_t v) {
-          smem_update(A.op[j], L.width[j], mine + offs[j] + (int64_t)gr * L.width[j], v);
-        });
-      else
-        warp_aggregate<kBatch>(A, cc, ok, gid[u], cv, u, row[u],
-                               [&](int j, int32_t gr, int64_t v) { agg_atomic(A.op[j], &A.out[j][gr], v); });
+      ok[u] = valid[u] && gid[u] >= 0 && gid[u] < g;
+    }
+    for (int j = 0; j < A.n; ++j) {
+      unsigned char* base = mine + offs[j];
+      int64_t* gout = A.out[j];
+      slot_dispatch(s_code[j], [&](auto U) {
+        using Up = decltype(U);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          if (!ok[u]) continue;
+          const int64_t v = Up::template value<kBatch>(A, j, cv, u, row[u]);
+          if (use_smem)
+            Up::apply(base + (int64_t)gid[u] * Up::kWidth, v);
+          else
+            agg_atomic(A.op[j], &gout[gid[u]], v);
+        }
+      });
+    }
+    if (split && ++step == epoch_steps) {
+      step = 0;
+      __syncthreads();
+      fold_split();
+      __syncthreads();
     }
   }
   if (lost) set_status(err, GJ_ERR_CAPACITY);  // a key whose insert failed (reported by stage 1)
   if (!use_smem) return;
   __syncthreads();
+  if (split) fold_split();
   for (int j = 0; j < A.n; ++j) {
-    const int op = A.op[j], w = L.width[j];
+    const int op = A.op[j], w = L.width[j], form = s_code[j] & 3;
+    if (form == kSlotSplit) continue;
     const int64_t idv = agg_identity(op);
     for (int64_t s = threadIdx.x; s < g; s += blockDim.x) {
-      int64_t v = smem_read(op, w, s_agg + offs[j] + s * w);
-      for (int c = 1; c < ncopy; ++c) v = agg_combine(op, v, smem_read(op, w, s_agg + c * copy_bytes + offs[j] + s * w));
+      int64_t v = slot_read(op, form, s_agg + offs[j] + s * w);
+      for (int c = 1; c < ncopy; ++c) v = agg_combine(op, v, slot_read(op, form, s_agg + c * copy_bytes + offs[j] + s * w));
       if (w == 4 && op == GJ_AGG_MIN && v == INT32_MAX) continue;
       if (w == 4 && op == GJ_AGG_MAX && v == INT32_MIN) continue;
       if (v == idv) continue;
       agg_atomic(op, &A.out[j][s], v);
     }
   }
+}
+
+// ---------------------------------------------------------------- HGB, few groups
+// When the groups hint says at most 32 groups, a single pass aggregates without
+// the dictionary pass and without atomics: each block keeps a 64-slot
+// shared-memory table of the keys it has seen (tagged 64-bit words, at most 32
+// keys), and every warp keeps, per slot, the COUNT and the SUM/MIN/MAX of each
+// cached 4-byte value column in registers -- lane l owns slots l and l + 32.
+// In a warp step (one row per lane) lane l finds the lanes whose row is in its
+// slot from six ballots on the slot number and pulls their values with
+// shuffles. Blocks leave their per-slot results in scratch; one block merges
+// them into the dense result (at most kTinyMerge groups). A block that meets a
+// 33rd key, or a merge that meets too many, sets `overflow` and the general
+// HGB kernels, which test it, run instead.
+constexpr int kTinySlots = 64;
+constexpr int kTinyKeys = 32;
+constexpr int kTinyMerge = 1024;
+
+struct TinyPart {  // one slot of one block: its key tag and the per-column results
+  unsigned long long tag;
+  unsigned int count;
+  int32_t pad;
+  int64_t sum[kColCache];
+  int32_t mn[kColCache];
+  int32_t mx[kColCache];
+};
+
+template <typename K>
+__global__ void __launch_bounds__(1024, 1) hgb_tiny_kernel(const K* __restrict__ key, int64_t n, ColCache cc,
+                                                           TinyPart* __restrict__ parts, int* overflow) {
+  __shared__ unsigned long long s_tab[kTinySlots];
+  __shared__ int s_nkeys;
+  __shared__ unsigned int s_cnt[kTinySlots];
+  __shared__ long long s_sum[kColCache][kTinySlots];
+  __shared__ int s_mn[kColCache][kTinySlots];
+  __shared__ int s_mx[kColCache][kTinySlots];
+  const unsigned long long empty = seen_empty<K>();
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < kTinySlots) {
+    s_tab[tid] = empty;
+    s_cnt[tid] = 0;
+    for (int c = 0; c < kColCache; ++c) {
+      s_sum[c][tid] = 0;
+      s_mn[c][tid] = INT32_MAX;
+      s_mx[c][tid] = INT32_MIN;
+    }
+  }
+  if (tid == 0) s_nkeys = 0;
+  __syncthreads();
+  // lane-owned results of slots lane and lane + 32
+  unsigned int cnt[2] = {0u, 0u};
+  int64_t sum[2][kColCache];
+  int32_t mn[2][kColCache], mx[2][kColCache];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int c = 0; c < kColCache; ++c) {
+      sum[h][c] = 0;
+      mn[h][c] = INT32_MAX;
+      mx[h][c] = INT32_MIN;
+    }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bail = false;
+  // the loop bound is the block's first row: every thread runs the same steps
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i - tid < n; i += stride) {
+    const bool valid = i < n;
+    const K k = valid ? __ldcs(key + i) : K(0);
+    int32_t v[kColCache];
+#pragma unroll
+    for (int c = 0; c < kColCache; ++c) v[c] = (valid && c < cc.n) ? __ldcs(cc.src[c] + i) : 0;
+    int slot = -1;
+    if (valid) {
+      const unsigned long long tag = seen_tag<K>(k);
+      if (tag != empty) {
+        uint32_t sl = (uint32_t)KeyTraits<K>::hash64(k) & (kTinySlots - 1);
+        for (int p = 0; p < kTinySlots; ++p) {
+          unsigned long long w = ((volatile unsigned long long*)s_tab)[sl];
+          if (w == empty) {
+            w = atomicCAS(&s_tab[sl], empty, tag);
+            if (w == empty) {
+              if (atomicAdd(&s_nkeys, 1) >= kTinyKeys) bail = true;
+              slot = (int)sl;
+              break;
+            }
+          }
+          if (w == tag) {
+            slot = (int)sl;
+            break;
+          }
+          sl = (sl + 1) & (kTinySlots - 1);
+        }
+      }
+      if (slot < 0) bail = true;  // INT64_MIN as an 8-byte key, or a full table
+    }
+    if (__syncthreads_or(bail)) break;  // too many keys for this path
+    // the lanes whose row is in slot lane (h = 0) and slot lane + 32 (h = 1)
+    unsigned m0 = __ballot_sync(0xffffffffu, slot >= 0), m1 = m0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const unsigned bb = __ballot_sync(0xffffffffu, (slot >> b) & 1);
+      const unsigned sel = ((lane >> b) & 1) ? bb : ~bb;
+      m0 &= sel;
+      m1 &= sel;
+    }
+    const unsigned b5 = __ballot_sync(0xffffffffu, (slot >> 5) & 1);
+    m0 &= ~b5;
+    m1 &= b5;
+    cnt[0] += __popc(m0);
+    cnt[1] += __popc(m1);
+    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)max(__popc(m0), __popc(m1)));
+    for (int r = 0; r < rounds; ++r) {
+      const int s0 = m0 ? __ffs(m0) - 1 : lane, s1 = m1 ? __ffs(m1) - 1 : lane;
+#pragma unroll
+      for (int c = 0; c < kColCache; ++c) {
+        const int32_t x0 = __shfl_sync(0xffffffffu, v[c], s0), x1 = __shfl_sync(0xffffffffu, v[c], s1);
+        if (m0) {
+          sum[0][c] += x0;
+          mn[0][c] = min(mn[0][c], x0);
+          mx[0][c] = max(mx[0][c], x0);
+        }
+        if (m1) {
+          sum[1][c] += x1;
+          mn[1][c] = min(mn[1][c], x1);
+          mx[1][c] = max(mx[1][c], x1);
+        }
+      }
+      m0 &= m0 - 1;
+      m1 &= m1 - 1;
+    }
+  }
+  if (s_nkeys > kTinyKeys || __syncthreads_or(bail)) {
+    if (tid == 0) atomicExch(overflow, 1);
+    return;
+  }
+  // the warps' results into the block's slots, then the block's slots out
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int sl = lane + 32 * h;
+    if (cnt[h] == 0) continue;
+    atomicAdd(&s_cnt[sl], cnt[h]);
+#pragma unroll
+    for (int c = 0; c < kColCache; ++c) {
+      atomicAdd((unsigned long long*)&s_sum[c][sl], (unsigned long long)sum[h][c]);
+      atomicMin(&s_mn[c][sl], mn[h][c]);
+      atomicMax(&s_mx[c][sl], mx[h][c]);
+    }
+  }
+  __syncthreads();
+  if (tid < kTinySlots) {
+    TinyPart t{};
+    t.tag = s_cnt[tid] ? s_tab[tid] : empty;
+    t.count = s_cnt[tid];
+    for (int c = 0; c < kColCache; ++c) {
+      t.sum[c] = s_sum[c][tid];
+      t.mn[c] = s_mn[c][tid];
+      t.mx[c] = s_mx[c][tid];
+    }
+    parts[(int64_t)blockIdx.x * kTinySlots + tid] = t;
+  }
+}
+
+// Merges the blocks' slots (one block): dense group ids in order of first
+// appearance, the aggregates of Aggs from the per-column results, g into
+// *ngroups. Sets `overflow` instead when the union of keys is too large.
+template <typename K>
+__global__ void __launch_bounds__(1024) hgb_tiny_merge_kernel(const TinyPart* __restrict__ parts, int nparts,
+                                                              Aggs A, ColCache cc, K* __restrict__ out_keys,
+                                                              int64_t cap, int64_t* ngroups, int* overflow, int* err) {
+  __shared__ unsigned long long s_key[2 * kTinyMerge];  // tags
+  __shared__ int s_id[2 * kTinyMerge];
+  __shared__ int s_n;
+  const unsigned long long empty = seen_empty<K>();
+  if (*(volatile int*)overflow) return;
+  for (int j = threadIdx.x; j < 2 * kTinyMerge; j += blockDim.x) {
+    s_key[j] = empty;
+    s_id[j] = -1;
+  }
+  if (threadIdx.x == 0) s_n = 0;
+  __syncthreads();
+  // ids: one thread per slot entry inserts the tag; the inserting thread takes the id
+  for (int e = threadIdx.x; e < nparts * kTinySlots; e += blockDim.x) {
+    const unsigned long long tag = parts[e].tag;
+    if (tag == empty) continue;
+    uint32_t sl = (uint32_t)(tag * 0x9e3779b97f4a7c15ull >> 40) & (2 * kTinyMerge - 1);
+    for (int p = 0; p < 2 * kTinyMerge; ++p) {
+      const unsigned long long w = atomicCAS(&s_key[sl], empty, tag);
+      if (w == empty) {
+        s_id[sl] = atomicAdd(&s_n, 1);
+        break;
+      }
+      if (w == tag) break;
+      sl = (sl + 1) & (2 * kTinyMerge - 1);
+    }
+  }
+  __syncthreads();
+  const int g = s_n;
+  if (g > kTinyMerge) {
+    if (threadIdx.x == 0) atomicExch(overflow, 1);
+    return;
+  }
+  // starting values, then every entry combined into its group (64-bit atomics on
+  // the result; at most nparts * 64 entries)
+  for (int t = threadIdx.x; t < g * A.n; t += blockDim.x) {
+    const int j = t / g, id = t - j * g;
+    if (id < cap) A.out[j][id] = agg_identity(A.op[j]);
+  }
+  for (int sl = threadIdx.x; sl < 2 * kTinyMerge; sl += blockDim.x) {
+    if (s_key[sl] == empty) continue;
+    const int id = s_id[sl];
+    const unsigned long long tag = s_key[sl];
+    const K k = sizeof(K) == 4 ? (K)(int32_t)(uint32_t)tag : (K)(int64_t)tag;
+    if (id < cap)
+      out_keys[id] = k;
+    else
+      set_status(err, GJ_ERR_CAPACITY);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nparts * kTinySlots; e += blockDim.x) {
+    const TinyPart& t = parts[e];
+    if (t.tag == empty) continue;
+    uint32_t sl = (uint32_t)(t.tag * 0x9e3779b97f4a7c15ull >> 40) & (2 * kTinyMerge - 1);
+    while (s_key[sl] != t.tag) sl = (sl + 1) & (2 * kTinyMerge - 1);
+    const int id = s_id[sl];
+    if (id >= cap) continue;
+    for (int j = 0; j < A.n; ++j) {
+      const int op = A.op[j], c = cc.slot[j];
+      const int64_t v = op == GJ_AGG_COUNT ? (int64_t)t.count
+                        : op == GJ_AGG_SUM ? t.sum[c]
+                        : op == GJ_AGG_MIN ? (int64_t)t.mn[c] : (int64_t)t.mx[c];
+      agg_atomic(op, &A.out[j][id], v);
+    }
+  }
+  if (threadIdx.x == 0) *ngroups = g;
 }
 
 // ================================================================ SGB
@@ -801,9 +1115,11 @@ __global__ void __launch_bounds__(kSegWarps * 32, 2) sgb_reduce_kernel(const K* 
 // a shared-memory table sized to the partition (a slot holds the partition row +
 // 1 of its key's first row; keys are compared in global memory, where the small
 // partition stays cached), gives the keys dense local ids in slot order,
-// aggregates every row into shared-memory slots by local id (warp_aggregate:
-// rows of one key in a warp are combined before the atomics), then reserves its
-// output rows from the global group counter and writes them with plain stores.
+// reserves the round's output rows from the global group counter, aggregates
+// every row into shared-memory slots by local id (one copy per warp, or per few
+// warps, when the round's groups leave room; 32-bit atomics only, SUMs split and
+// folded into the output rows every kSplitRows rows) and writes the rest of the
+// output rows with plain stores.
 // A partition whose distinct keys exceed the block's group capacity C is split by
 // a second hash into two halves, recursively, each processed as above.
 constexpr int kPgbThreads = 512;
@@ -846,6 +1162,7 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
   K* s_key = (K*)(s_raw + pgb_key_off<K>(C));
   unsigned char* s_agg = s_raw + pgb_agg_off<K>(C);
   __shared__ int64_t offs[kMaxAggs];
+  __shared__ int s_code[kMaxAggs];
   __shared__ int s_wsum[kPgbThreads / 32];
   __shared__ int s_count;
   __shared__ unsigned long long s_base;
@@ -861,18 +1178,13 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
   int tslots = 64;  // table slots: about twice the rows, at most 2C
   while (tslots < 2 * C && tslots < 2 * rows) tslots <<= 1;
   if (tid == 0) {
-    int64_t o = 0;
-    for (int q = 0; q < A.n; ++q) {
-      const int j = L.order[q];
-      offs[j] = o;
-      o += (int64_t)C * L.width[j];
-    }
     s_stack_q[0] = 0;
     s_stack_r[0] = 0;
     s_top = 1;
   }
   __syncthreads();
   bool over_cap = false;
+  const int nwarps = blockDim.x >> 5;
   // rounds (q, r): the rows whose second hash has r in its low q bits
   while (s_top > 0) {
     const int q = s_stack_q[s_top - 1];
@@ -961,55 +1273,108 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
         }
       }
     }
-    for (int jq = 0; jq < A.n; ++jq)
-      for (int l = tid; l < count; l += blockDim.x)
-        smem_init(A.op[jq], L.width[jq], s_agg + offs[jq] + (int64_t)l * L.width[jq]);
+    // copies of the round's slots: as many (up to one per warp) as fit in C groups
+    int ncopy = 1;
+    while (ncopy < nwarps && 2 * ncopy * count <= C) ncopy *= 2;
+    const int cc_cap = C / ncopy;  // groups per copy
+    const int64_t copy_bytes = (int64_t)cc_cap * L.bytes_per_group;
+    if (tid == 0) {
+      int64_t o = 0;
+      for (int q2 = 0; q2 < A.n; ++q2) {
+        const int j = L.order[q2];
+        offs[j] = o;
+        o += (int64_t)cc_cap * L.width[j];
+      }
+      s_base = atomicAdd(ngroups, (unsigned long long)count);  // the round's output rows
+    }
+    if (tid < A.n) s_code[tid] = slot_code(A.op[tid], A.op[tid] == GJ_AGG_COUNT ? -1 : cc.slot[tid],
+                                           slot_form(A, cc, tid, true));
     __syncthreads();
-    // ---- aggregate the round's rows by local id (the loop bound is uniform:
-    // warp_aggregate needs every lane of the warp)
-    for (int64_t b0 = r0; b0 < r1; b0 += (int64_t)kBatch * blockDim.x) {
-      int64_t row[kBatch];
-      bool valid[kBatch];
-      int32_t lid[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        row[u] = b0 + (int64_t)u * blockDim.x + tid;
-        valid[u] = row[u] < r1;
-        lid[u] = -1;
-        if (!valid[u]) continue;
-        const K k = key[row[u]];
-        if (pgb_sub<K>(k, q) != round) continue;
-        uint32_t sl = pgb_slot<K>(k, pbits, tslots);
-        for (int probe = 0; probe < tslots; ++probe) {
-          if (s_slot[sl] == 0) break;
-          const int l = s_lid[sl];
-          if (s_key[l] == k) {
-            lid[u] = l;
-            break;
+    const int64_t base = (int64_t)s_base;
+    for (int c = 0; c < ncopy; ++c)
+      for (int jq = 0; jq < A.n; ++jq)
+        for (int l = tid; l < count; l += blockDim.x)
+          smem_init(A.op[jq], L.width[jq], s_agg + c * copy_bytes + offs[jq] + (int64_t)l * L.width[jq]);
+    // split SUMs accumulate in the output rows, folded in every kSplitRows rows
+    for (int j = 0; j < A.n; ++j)
+      if ((s_code[j] & 3) == kSlotSplit)
+        for (int l = tid; l < count && base + l < cap; l += blockDim.x) A.out[j][base + l] = 0;
+    __syncthreads();
+    auto fold_split = [&]() {
+      for (int j = 0; j < A.n; ++j) {
+        if ((s_code[j] & 3) != kSlotSplit) continue;
+        for (int l = tid; l < count; l += blockDim.x) {
+          int64_t v = 0;
+          for (int c = 0; c < ncopy; ++c) {
+            unsigned char* pp = s_agg + c * copy_bytes + offs[j] + (int64_t)l * 8;
+            v += slot_read(GJ_AGG_SUM, kSlotSplit, pp);
+            *(int64_t*)pp = 0;
           }
-          sl = (sl + 1) & (uint32_t)(tslots - 1);
+          if (base + l < cap) A.out[j][base + l] += v;  // this block owns the row
         }
       }
-      int32_t cv[kColCache][kBatch];
-      load_cached<kBatch>(cc, row, valid, cv);
+    };
+    unsigned char* my_agg = s_agg + (warp & (ncopy - 1)) * copy_bytes;
+    // ---- aggregate the round's rows by local id, in epochs of kSplitRows rows
+    for (int64_t e0 = r0; e0 < r1; e0 += kSplitRows) {
+      const int64_t e1 = min64(r1, e0 + kSplitRows);
+      for (int64_t b0 = e0; b0 < e1; b0 += (int64_t)kBatch * blockDim.x) {
+        int64_t row[kBatch];
+        bool valid[kBatch];
+        int32_t lid[kBatch];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u)
-        warp_aggregate<kBatch>(A, cc, lid[u] >= 0, lid[u], cv, u, row[u], [&](int j, int32_t l, int64_t v) {
-          smem_update(A.op[j], L.width[j], s_agg + offs[j] + (int64_t)l * L.width[j], v);
-        });
+        for (int u = 0; u < kBatch; ++u) {
+          row[u] = b0 + (int64_t)u * blockDim.x + tid;
+          valid[u] = row[u] < e1;
+          lid[u] = -1;
+          if (!valid[u]) continue;
+          const K k = key[row[u]];
+          if (pgb_sub<K>(k, q) != round) continue;
+          uint32_t sl = pgb_slot<K>(k, pbits, tslots);
+          for (int probe = 0; probe < tslots; ++probe) {
+            if (s_slot[sl] == 0) break;
+            const int l = s_lid[sl];
+            if (s_key[l] == k) {
+              lid[u] = l;
+              break;
+            }
+            sl = (sl + 1) & (uint32_t)(tslots - 1);
+          }
+        }
+        int32_t cv[kColCache][kBatch];
+        load_cached<kBatch>(cc, row, valid, cv);
+        for (int j = 0; j < A.n; ++j) {
+          unsigned char* sb = my_agg + offs[j];
+          slot_dispatch(s_code[j], [&](auto U) {
+            using Up = decltype(U);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+              if (lid[u] >= 0)
+                Up::apply(sb + (int64_t)lid[u] * Up::kWidth, Up::template value<kBatch>(A, j, cv, u, row[u]));
+          });
+        }
+      }
+      __syncthreads();
+      fold_split();
+      __syncthreads();
     }
-    __syncthreads();
-    // ---- the round's groups: output rows reserved from the global counter
-    if (tid == 0) s_base = atomicAdd(ngroups, (unsigned long long)count);
-    __syncthreads();
+    // ---- the round's groups: keys and the other aggregates, copies combined
     for (int l = tid; l < count; l += blockDim.x) {
-      const int64_t o = (int64_t)s_base + l;
+      const int64_t o = base + l;
       if (o >= cap) {
         over_cap = true;
         continue;
       }
       out_keys[o] = s_key[l];
-      for (int j = 0; j < A.n; ++j) A.out[j][o] = smem_read(A.op[j], L.width[j], s_agg + offs[j] + (int64_t)l * L.width[j]);
+      for (int j = 0; j < A.n; ++j) {
+        const int form = s_code[j] & 3;
+        if (form == kSlotSplit) continue;
+        const unsigned char* sl = s_agg + offs[j] + (int64_t)l * L.width[j];
+        int64_t v = slot_read(A.op[j], form, sl);
+        // copies a group never reached hold the identity, which combining leaves out
+        for (int c = 1; c < ncopy; ++c) v = agg_combine(A.op[j], v, slot_read(A.op[j], form, sl + c * copy_bytes));
+        A.out[j][o] = v;
+      }
     }
     __syncthreads();
   }
@@ -1123,6 +1488,33 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   if ((st = cuda_check(cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), s))) != GJ_OK) return st;
   if (n == 0) return GJ_OK;
 
+  // HGB with at most 32 expected groups: the few-groups pass first; the general
+  // kernels below run only if it reports overflow
+  int* gate = nullptr;
+  if (variant == GJ_GB_HGB && opt->groups_hint > 0 && opt->groups_hint <= kTinyKeys) {
+    Aggs A0 = make_aggs(in, nagg, ops, op_col, out_aggs, in->cols);
+    const ColCache cc0 = make_col_cache(A0);
+    bool eligible = true;
+    for (int j = 0; j < nagg; ++j)
+      if (ops[j] != GJ_AGG_COUNT && (A0.size[j] != 4 || cc0.slot[j] < 0)) eligible = false;
+    if (eligible) {
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 2));
+      TinyPart* parts = scr.get_as<TinyPart>((size_t)blocks * kTinySlots);
+      gate = scr.get_as<int>(1);
+      if (scr.failed()) return GJ_ERR_OOM;
+      if ((st = cuda_check(cudaMemsetAsync(gate, 0, sizeof(int), s))) != GJ_OK) return st;
+      {
+        LaunchScope ls(ctx, KK_HGB_AGG);
+        hgb_tiny_kernel<K><<<blocks, 1024, 0, s>>>((const K*)in->key, n, cc0, parts, gate);
+      }
+      {
+        LaunchScope ls(ctx, KK_HGB_AGG);
+        hgb_tiny_merge_kernel<K><<<1, 1024, 0, s>>>(parts, blocks, A0, cc0, (K*)out_keys, cap, d_ngroups, gate,
+                                                     ctx.d_status);
+      }
+    }
+  }
+
   // HGB and SGB-DE share the dictionary of Alg. 1, stage 1: a table of (key, dense
   // id) entries sized for twice the expected groups (the hint, else n), filled
   // by one pass over the keys; out_keys receives the dictionary (id -> key).
@@ -1136,16 +1528,20 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     if (scr.failed()) return GJ_ERR_OOM;
     if ((st = cuda_check(cudaMemsetAsync(ht, 0, sizeof(HEntry<K>) * slots, s))) != GJ_OK) return st;
     LaunchScope ls(ctx, KK_HGB_GROUP_ID);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 511) / 512, (int64_t)ctx.num_sms * 4));
-    hgb_dict_kernel<K><<<blocks, 512, 0, s>>>((const K*)in->key, n, ht, slots - 1, (unsigned long long*)d_ngroups,
-                                              (K*)out_keys, cap, ctx.d_status);
+    // one block per SM with its key cache
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms));
+    const int cache_bytes = kSeenSlots * (int)sizeof(unsigned long long);
+    if ((st = ensure_smem_attr(ctx, (const void*)hgb_dict_kernel<K>, cache_bytes)) != GJ_OK) return st;
+    hgb_dict_kernel<K><<<blocks, 1024, cache_bytes, s>>>((const K*)in->key, n, ht, slots - 1,
+                                                         (unsigned long long*)d_ngroups, (K*)out_keys, cap, gate,
+                                                         ctx.d_status);
   }
 
   if (variant == GJ_GB_HGB) {
     Aggs A = make_aggs(in, nagg, ops, op_col, out_aggs, in->cols);
     {
       LaunchScope ls(ctx, KK_AGG_INIT);
-      agg_init_kernel<<<ctx.num_sms * 4, 256, 0, s>>>(A, d_ngroups, cap);
+      agg_init_kernel<<<ctx.num_sms * 4, 256, 0, s>>>(A, d_ngroups, cap, gate);
     }
     SmemAggLayout L{};
     int q = 0;
@@ -1163,7 +1559,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     {
       LaunchScope ls(ctx, KK_HGB_AGG);
       hgb_aggregate_kernel<K><<<ctx.num_sms, 1024, budget, s>>>((const K*)in->key, n, ht, slots - 1, A,
-                                                                 make_col_cache(A), L, d_ngroups, cap, budget,
+                                                                 make_col_cache(A), L, d_ngroups, cap, budget, gate,
                                                                  ctx.d_status);
     }
     return cuda_check(cudaGetLastError());

@@ -322,6 +322,141 @@ __device__ __forceinline__ void emit_cols(const JoinIO& io, int c, int g, bool r
   }
 }
 
+// Output offset of a probe unit (decoupled look-back over units) and the
+// materialisation of its matches: s_midx[r] is the build row of unit row r (or
+// -1). Every warp owns a contiguous range of the unit and writes it without
+// block barriers, all loads of a group of columns in flight before its stores.
+// Called by all threads of the block after s_midx is complete.
+template <typename K>
+__device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_t u0, int un, int64_t unit,
+                                              int64_t nunits, const int32_t* s_midx, const JoinIO& io,
+                                              uint64_t* unit_status, int* err, uint32_t* s_wcnt, uint64_t* s_base_p) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint64_t& s_base = *s_base_p;
+  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
+  const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
+  uint32_t cnt = 0;
+  for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_wcnt[warp] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
+    if (lane == 0) {
+      s_base = excl;
+      if (unit == nunits - 1 && io.d_count) *io.d_count = (int64_t)(excl + tot);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: each warp materialises its range, no block barriers
+  int64_t pos = (int64_t)s_base;
+  for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+  const int64_t cap = io.cap;
+  const unsigned lt = (1u << lane) - 1;
+  const int ncols = io.nr_cols + io.ns_cols;
+  bool overflow = false;
+  for (int b0 = w0; b0 < wend; b0 += 32 * kEmitU) {
+    uint32_t o[kEmitU], ridx[kEmitU], sidx[kEmitU];
+    bool ok[kEmitU];
+#pragma unroll
+    for (int j = 0; j < kEmitU; ++j) {
+      const int r = b0 + j * 32 + lane;
+      const int32_t m = r < wend ? s_midx[r] : -1;
+      const unsigned bal = __ballot_sync(0xffffffffu, m >= 0);
+      const int64_t oo = pos + __popc(bal & lt);
+      pos += __popc(bal);
+      ok[j] = m >= 0 && oo < cap;
+      overflow |= m >= 0 && oo >= cap;
+      o[j] = (uint32_t)oo;
+      ridx[j] = (uint32_t)m;
+      sidx[j] = (uint32_t)(u0 + r);
+    }
+    if (io.r_tid) {
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) ridx[j] = ok[j] ? (uint32_t)__ldg(io.r_tid + ridx[j]) : 0u;
+    }
+    if (io.s_tid) {
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) sidx[j] = ok[j] ? (uint32_t)__ldcs(io.s_tid + sidx[j]) : 0u;
+    }
+    {
+      K kv[kEmitU];
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j) kv[j] = skey[ok[j] ? u0 + b0 + j * 32 + lane : u0];
+      K* __restrict__ tk = (K*)io.tkey;
+#pragma unroll
+      for (int j = 0; j < kEmitU; ++j)
+        if (ok[j]) __stcs(tk + o[j], kv[j]);
+    }
+    if (io.narrow4) {
+      // every column 4 bytes wide, at most 4 per side: all loads of the step in flight together
+      int32_t vr[4][kEmitU], vs[4][kEmitU];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t* __restrict__ rs = (const int32_t*)io.rsrc[q < io.nr_cols ? q : 0];
+        const int32_t* __restrict__ ss = (const int32_t*)io.ssrc[q < io.ns_cols ? q : 0];
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          vr[q][j] = (q < io.nr_cols && !io.r_zip) ? __ldg(rs + (ok[j] ? ridx[j] : 0u)) : 0;
+          vs[q][j] = (q < io.ns_cols && !io.s_zip) ? __ldcs(ss + (ok[j] ? sidx[j] : 0u)) : 0;
+        }
+      }
+      if (io.r_zip) {
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          const int4 v = __ldg(io.r_zip + (ok[j] ? ridx[j] : 0u));
+          vr[0][j] = v.x;
+          vr[1][j] = v.y;
+          vr[2][j] = v.z;
+          vr[3][j] = v.w;
+        }
+      }
+      if (io.s_zip) {
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          const int4 v = __ldcs(io.s_zip + (ok[j] ? sidx[j] : 0u));
+          vs[0][j] = v.x;
+          vs[1][j] = v.y;
+          vs[2][j] = v.z;
+          vs[3][j] = v.w;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int32_t* __restrict__ dr = (int32_t*)io.tcols[q < io.nr_cols ? q : 0];
+        int32_t* __restrict__ ds = (int32_t*)io.tcols[io.nr_cols + (q < io.ns_cols ? q : 0)];
+#pragma unroll
+        for (int j = 0; j < kEmitU; ++j) {
+          if (q < io.nr_cols && ok[j]) __stcs(dr + o[j], vr[q][j]);
+          if (q < io.ns_cols && ok[j]) __stcs(ds + o[j], vs[q][j]);
+        }
+      }
+      continue;
+    }
+    int c = 0;
+    while (c < ncols) {
+      const bool rside = c < io.nr_cols;
+      const int size = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
+      const int gmax = size == 8 ? 2 : 4;
+      int g = 1;
+      while (g < gmax && c + g < ncols && (c + g < io.nr_cols) == rside &&
+             (rside ? io.rsize[c + g] : io.ssize[c + g - io.nr_cols]) == size)
+        ++g;
+      if (size == 8)
+        emit_cols<int64_t, 2, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
+      else
+        emit_cols<int32_t, 4, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
+      c += g;
+    }
+  }
+  if (overflow) set_status(err, GJ_ERR_CAPACITY);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) phj_unit_kernel(const K* __restrict__ rkey,
                                                             const int64_t* __restrict__ roff, int pbits,
@@ -471,130 +606,190 @@ __global__ void __launch_bounds__(kThreads, 4) phj_unit_kernel(const K* __restri
       a = b;
     }
   }
-
-  // ---- unit offset: per-warp match counts over warp-contiguous ranges, look-back
-  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
-  const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
-  uint32_t cnt = 0;
-  for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane == 0) s_wcnt[warp] = cnt;
+  // the last partition may have had no build rows: its -1 entries were written
+  // without a barrier after them
   __syncthreads();
-  if (warp == 0) {
-    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
+  phj_emit_unit<K>(skey, u0, un, unit, nunits, s_midx, io, unit_status, err, s_wcnt, &s_base);
+}
+
+// ---------------------------------------------------------------- PHJ, L2-sized partitions
+// With a large build side, one 8-bit hashed pass per side replaces the two passes
+// that shared-memory-sized partitions need. Each of the 256 build partitions R'_P
+// gets an open-addressing table in global memory at toff[P] (a power of two of
+// at least twice its rows, holding R' row + 1), built once; a probe unit of S'
+// rows of partition P looks its keys up there. R'_P and its table (a few MB) stay
+// in the 129 MB L2 while the units of S'_P run, so the gathers from R'_P are
+// clustered in L2 the way GFTR clusters them in shared memory for small
+// partitions. Output offsets and materialisation are those of phj_unit_kernel.
+constexpr int kL2Parts = 256;
+constexpr int kL2Bits = 8;
+
+// toff[P] = sum of the table sizes of partitions < P, toff[kL2Parts] = the total.
+__global__ void __launch_bounds__(kL2Parts) l2_table_offsets_kernel(const int64_t* __restrict__ roff,
+                                                                   int64_t* __restrict__ toff) {
+  __shared__ int64_t s[kL2Parts];
+  const int p = threadIdx.x;
+  const int64_t rows = roff[p + 1] - roff[p];
+  int64_t sz = 2;
+  while (sz < 2 * rows) sz <<= 1;
+  s[p] = sz;
+  __syncthreads();
+  for (int o = 1; o < kL2Parts; o <<= 1) {
+    const int64_t v = p >= o ? s[p - o] : 0;
+    __syncthreads();
+    s[p] += v;
+    __syncthreads();
+  }
+  toff[p + 1] = s[p];
+  if (p == 0) toff[0] = 0;
+}
+
+__global__ void l2_table_clear_kernel(int32_t* __restrict__ table, const int64_t* __restrict__ toff, int words) {
+  const int64_t total = toff[kL2Parts] * words;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < total; i += stride) {
+    if (i + 4 <= total)
+      *reinterpret_cast<int4*>(table + i) = make_int4(0, 0, 0, 0);  // sizes are powers of two >= 2: 16-byte runs
+    else
+      for (int64_t e = i; e < total; ++e) table[e] = 0;
+  }
+}
+
+// Table entries: for 4-byte keys one 64-bit word, (row + 1) << 32 | key, claimed
+// by a single compare-and-swap, so a probe reads key and row in one access; for
+// 8-byte keys a 32-bit row + 1 with the key compared in R'.
+template <typename K>
+struct L2Slot;
+template <>
+struct L2Slot<int32_t> {
+  using W = unsigned long long;
+  static constexpr int kWords = 2;  // int32 words per entry
+  static __device__ __forceinline__ W make(int32_t k, int64_t i) {
+    return ((W)(uint32_t)(i + 1) << 32) | (W)(uint32_t)k;
+  }
+};
+template <>
+struct L2Slot<int64_t> {
+  using W = int32_t;
+  static constexpr int kWords = 1;
+};
+
+// Build: blocks take chunks of R' in order from a counter, so the tables being
+// filled at any time are those of a few neighbouring partitions (in L2).
+constexpr int kL2BuildChunk = 4096;
+template <typename K>
+__global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rkey, int64_t nr,
+                                                       const int64_t* __restrict__ toff, int32_t* __restrict__ table,
+                                                       int* chunk_counter, int* err) {
+  __shared__ int64_t s_chunk;
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(chunk_counter, 1);
+    __syncthreads();
+    const int64_t c0 = s_chunk * kL2BuildChunk;
+    __syncthreads();
+    if (c0 >= nr) return;
+    const int64_t c1 = min64(nr, c0 + kL2BuildChunk);
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+      const K k = rkey[i];
+      const uint64_t h = KeyTraits<K>::hash64(k);
+      const int P = (int)(h & (kL2Parts - 1));
+      const int64_t base = toff[P];
+      const uint64_t msk = (uint64_t)(toff[P + 1] - base) - 1;
+      uint64_t sl = (h >> kL2Bits) & msk;
+      if constexpr (sizeof(K) == 4) {
+        auto* t = reinterpret_cast<unsigned long long*>(table) + base;
+        const unsigned long long w = L2Slot<int32_t>::make((int32_t)k, i);
+        for (uint64_t probe = 0; probe <= msk; ++probe) {
+          const unsigned long long prev = atomicCAS(&t[sl], 0ull, w);
+          if (prev == 0ull) break;
+          if ((int32_t)(uint32_t)prev == (int32_t)k) {
+            set_status(err, GJ_ERR_DUPLICATE_KEY);
+            break;
+          }
+          sl = (sl + 1) & msk;
+        }
+      } else {
+        int32_t* t = table + base;
+        for (uint64_t probe = 0; probe <= msk; ++probe) {
+          const int prev = atomicCAS(&t[sl], 0, (int)(i + 1));
+          if (prev == 0) break;
+          if (rkey[prev - 1] == k) {
+            set_status(err, GJ_ERR_DUPLICATE_KEY);
+            break;
+          }
+          sl = (sl + 1) & msk;
+        }
+      }
+    }
+  }
+}
+
+// The R' row of key k in the table of its partition, or -1.
+template <typename K>
+__device__ __forceinline__ int32_t l2_find(const K* __restrict__ rkey, const int32_t* __restrict__ table,
+                                           int64_t base, uint64_t msk, uint64_t sl, K k) {
+  if constexpr (sizeof(K) == 4) {
+    const auto* t = reinterpret_cast<const unsigned long long*>(table) + base;
+    for (uint64_t probe = 0; probe <= msk; ++probe) {
+      const unsigned long long w = __ldg(t + sl);
+      if (w == 0ull) return -1;
+      if ((int32_t)(uint32_t)w == (int32_t)k) return (int32_t)(w >> 32) - 1;
+      sl = (sl + 1) & msk;
+    }
+  } else {
+    const int32_t* t = table + base;
+    for (uint64_t probe = 0; probe <= msk; ++probe) {
+      const int v = __ldg(t + sl);
+      if (v == 0) return -1;
+      if (__ldg(rkey + v - 1) == k) return v - 1;
+      sl = (sl + 1) & msk;
+    }
+  }
+  return -1;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __restrict__ rkey,
+                                                                const int64_t* __restrict__ toff,
+                                                                const int32_t* __restrict__ table,
+                                                                const K* __restrict__ skey, int64_t ns, JoinIO io,
+                                                                uint64_t* unit_status, int* unit_counter,
+                                                                int64_t nunits, int* err) {
+  __shared__ int32_t s_midx[kUnitRows];
+  __shared__ int64_t s_toff[kL2Parts + 1];
+  __shared__ int64_t s_unit;
+  __shared__ uint32_t s_wcnt[kThreads / 32];
+  __shared__ uint64_t s_base;
+  const int t = threadIdx.x;
+  if (t == 0) s_unit = atomicAdd(unit_counter, 1);
+  for (int p = t; p <= kL2Parts; p += kThreads) s_toff[p] = toff[p];
+  __syncthreads();
+  const int64_t unit = s_unit;
+  if (unit >= nunits) return;
+  const int64_t u0 = unit * kUnitRows;
+  const int un = (int)min64(kUnitRows, ns - u0);
+  // every row's build row: kLook rows per thread in flight
+  constexpr int kLook = 4;
+  for (int r0 = 0; r0 < un; r0 += kThreads * kLook) {
+    K k[kLook];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
-    if (lane == 0) {
-      s_base = excl;
-      if (unit == nunits - 1 && io.d_count) *io.d_count = (int64_t)(excl + tot);
+    for (int q = 0; q < kLook; ++q) {
+      const int r = r0 + q * kThreads + t;
+      k[q] = r < un ? __ldcs(skey + u0 + r) : K(0);
+    }
+#pragma unroll
+    for (int q = 0; q < kLook; ++q) {
+      const int r = r0 + q * kThreads + t;
+      if (r >= un) continue;
+      const uint64_t h = KeyTraits<K>::hash64(k[q]);
+      const int P = (int)(h & (kL2Parts - 1));
+      const int64_t base = s_toff[P];  // in entries
+      const uint64_t msk = (uint64_t)(s_toff[P + 1] - s_toff[P]) - 1;
+      s_midx[r] = l2_find<K>(rkey, table, base, msk, (h >> kL2Bits) & msk, k[q]);
     }
   }
   __syncthreads();
-
-  // ---- phase 2: each warp materialises its range, no block barriers
-  int64_t pos = (int64_t)s_base;
-  for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
-  const int64_t cap = io.cap;
-  const unsigned lt = (1u << lane) - 1;
-  const int ncols = io.nr_cols + io.ns_cols;
-  bool overflow = false;
-  for (int b0 = w0; b0 < wend; b0 += 32 * kEmitU) {
-    uint32_t o[kEmitU], ridx[kEmitU], sidx[kEmitU];
-    bool ok[kEmitU];
-#pragma unroll
-    for (int j = 0; j < kEmitU; ++j) {
-      const int r = b0 + j * 32 + lane;
-      const int32_t m = r < wend ? s_midx[r] : -1;
-      const unsigned bal = __ballot_sync(0xffffffffu, m >= 0);
-      const int64_t oo = pos + __popc(bal & lt);
-      pos += __popc(bal);
-      ok[j] = m >= 0 && oo < cap;
-      overflow |= m >= 0 && oo >= cap;
-      o[j] = (uint32_t)oo;
-      ridx[j] = (uint32_t)m;
-      sidx[j] = (uint32_t)(u0 + r);
-    }
-    if (io.r_tid) {
-#pragma unroll
-      for (int j = 0; j < kEmitU; ++j) ridx[j] = ok[j] ? (uint32_t)__ldg(io.r_tid + ridx[j]) : 0u;
-    }
-    if (io.s_tid) {
-#pragma unroll
-      for (int j = 0; j < kEmitU; ++j) sidx[j] = ok[j] ? (uint32_t)__ldcs(io.s_tid + sidx[j]) : 0u;
-    }
-    {
-      K kv[kEmitU];
-#pragma unroll
-      for (int j = 0; j < kEmitU; ++j) kv[j] = skey[ok[j] ? u0 + b0 + j * 32 + lane : u0];
-      K* __restrict__ tk = (K*)io.tkey;
-#pragma unroll
-      for (int j = 0; j < kEmitU; ++j)
-        if (ok[j]) __stcs(tk + o[j], kv[j]);
-    }
-    if (io.narrow4) {
-      // every column 4 bytes wide, at most 4 per side: all loads of the step in flight together
-      int32_t vr[4][kEmitU], vs[4][kEmitU];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int32_t* __restrict__ rs = (const int32_t*)io.rsrc[q < io.nr_cols ? q : 0];
-        const int32_t* __restrict__ ss = (const int32_t*)io.ssrc[q < io.ns_cols ? q : 0];
-#pragma unroll
-        for (int j = 0; j < kEmitU; ++j) {
-          vr[q][j] = (q < io.nr_cols && !io.r_zip) ? __ldg(rs + (ok[j] ? ridx[j] : 0u)) : 0;
-          vs[q][j] = (q < io.ns_cols && !io.s_zip) ? __ldcs(ss + (ok[j] ? sidx[j] : 0u)) : 0;
-        }
-      }
-      if (io.r_zip) {
-#pragma unroll
-        for (int j = 0; j < kEmitU; ++j) {
-          const int4 v = __ldg(io.r_zip + (ok[j] ? ridx[j] : 0u));
-          vr[0][j] = v.x;
-          vr[1][j] = v.y;
-          vr[2][j] = v.z;
-          vr[3][j] = v.w;
-        }
-      }
-      if (io.s_zip) {
-#pragma unroll
-        for (int j = 0; j < kEmitU; ++j) {
-          const int4 v = __ldcs(io.s_zip + (ok[j] ? sidx[j] : 0u));
-          vs[0][j] = v.x;
-          vs[1][j] = v.y;
-          vs[2][j] = v.z;
-          vs[3][j] = v.w;
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int32_t* __restrict__ dr = (int32_t*)io.tcols[q < io.nr_cols ? q : 0];
-        int32_t* __restrict__ ds = (int32_t*)io.tcols[io.nr_cols + (q < io.ns_cols ? q : 0)];
-#pragma unroll
-        for (int j = 0; j < kEmitU; ++j) {
-          if (q < io.nr_cols && ok[j]) __stcs(dr + o[j], vr[q][j]);
-          if (q < io.ns_cols && ok[j]) __stcs(ds + o[j], vs[q][j]);
-        }
-      }
-      continue;
-    }
-    int c = 0;
-    while (c < ncols) {
-      const bool rside = c < io.nr_cols;
-      const int size = rside ? io.rsize[c] : io.ssize[c - io.nr_cols];
-      const int gmax = size == 8 ? 2 : 4;
-      int g = 1;
-      while (g < gmax && c + g < ncols && (c + g < io.nr_cols) == rside &&
-             (rside ? io.rsize[c + g] : io.ssize[c + g - io.nr_cols]) == size)
-        ++g;
-      if (size == 8)
-        emit_cols<int64_t, 2, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
-      else
-        emit_cols<int32_t, 4, kEmitU>(io, c, g, rside, rside ? ridx : sidx, o, ok);
-      c += g;
-    }
-  }
-  if (overflow) set_status(err, GJ_ERR_CAPACITY);
+  phj_emit_unit<K>(skey, u0, un, unit, nunits, s_midx, io, unit_status, err, s_wcnt, &s_base);
 }
 
 // ---------------------------------------------------------------- NPHJ
@@ -1140,7 +1335,7 @@ __global__ void __launch_bounds__(kThreads) group_emit_kernel(GroupSink G, int64
 }
 
 template <typename K>
-gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int variant, int bits, int bpp,
+gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int variant, int bits, int bpp, bool l2,
                      gj_table* T, int64_t cap, int64_t* d_count) {
   cudaStream_t s = ctx.stream;
   Scratch scr(s);
@@ -1368,6 +1563,31 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if (scr.failed()) return GJ_ERR_OOM;
   if ((st = cuda_check(cudaMemsetAsync(ustat, 0, sizeof(uint64_t) * nunits, s))) != GJ_OK) return st;
   if ((st = cuda_check(cudaMemsetAsync(ucounter, 0, sizeof(int), s))) != GJ_OK) return st;
+  if (l2) {
+    // one table per L2-sized build partition, then the probe units
+    int64_t* toff = scr.get_as<int64_t>(kL2Parts + 1);
+    constexpr int kW = L2Slot<K>::kWords;  // int32 words per entry
+    int32_t* table = scr.get_as<int32_t>(((size_t)4 * nr + 2 * kL2Parts) * kW);  // sizes < 4 rows + 2 each
+    int* bcounter = scr.get_as<int>(1);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = cuda_check(cudaMemsetAsync(bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
+    {
+      LaunchScope ls(ctx, KK_PART_BOUNDS);
+      l2_table_offsets_kernel<<<1, kL2Parts, 0, s>>>(roff, toff);
+    }
+    {
+      LaunchScope ls(ctx, KK_NPHJ_BUILD);
+      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((4 * nr + 1023) / 1024, (int64_t)ctx.num_sms * 8));
+      l2_table_clear_kernel<<<blocks, 256, 0, s>>>(table, toff, kW);
+      const int bblocks =
+          (int)std::max<int64_t>(1, std::min<int64_t>((nr + kL2BuildChunk - 1) / kL2BuildChunk, (int64_t)ctx.num_sms * 8));
+      l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk, nr, toff, table, bcounter, ctx.d_status);
+    }
+    LaunchScope ls(ctx, KK_PHJ_PROBE);
+    phj_l2_probe_kernel<K><<<(unsigned)nunits, kThreads, 0, s>>>(rk, toff, table, sk, ns, io, ustat, ucounter, nunits,
+                                                                  ctx.d_status);
+    return cuda_check(cudaGetLastError());
+  }
   const size_t dyn = phj_unit_smem_bytes<K>();
   if ((st = ensure_smem_attr(ctx, (const void*)phj_unit_kernel<K>, (int)dyn)) != GJ_OK) return st;
   LaunchScope ls(ctx, KK_PHJ_PROBE);
@@ -1580,9 +1800,14 @@ gj_status join_run(const Ctx& ctx, const gj_table* R, const gj_table* S, const g
                    int64_t cap, int64_t* d_count) {
   const int variant = resolve_join_variant(R, S, 0, opt, false);
   int bits = opt->radix_bits > 0 ? std::min(opt->radix_bits, 16) : choose_join_bits(R->n, 512);
+  // a build side that shared-memory partitions would need two passes for, but whose
+  // 256 partitions stay L2-sized: one pass per side and L2-resident tables
+  const bool l2 = (variant == GJ_JOIN_PHJ_TR || variant == GJ_JOIN_PHJ_UR) && opt->radix_bits <= 0 &&
+                  bits > kL2Bits && R->n <= (int64_t(1) << 27);
+  if (l2) bits = kL2Bits;
   if (R->key_type == GJ_I64)
-    return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
-  return join_typed<int32_t>(ctx, R, S, variant, bits, opt->bits_per_pass, T, cap, d_count);
+    return join_typed<int64_t>(ctx, R, S, variant, bits, opt->bits_per_pass, l2, T, cap, d_count);
+  return join_typed<int32_t>(ctx, R, S, variant, bits, opt->bits_per_pass, l2, T, cap, d_count);
 }
 
 }  // namespace gj

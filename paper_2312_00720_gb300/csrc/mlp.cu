@@ -4,11 +4,11 @@
 // the group-by decision tree of Fig. groupby-dt), which stay the fallback.
 //
 // Forward: one block of 64 threads per sample, thread j owns hidden unit j of
-// both layers; the 6 outputs are reduced by threads 0..5. Backward: each block
+// both layers; the 11 outputs are reduced by threads 0..10. Backward: each block
 // processes a fixed slice of the batch and accumulates its partial gradient in
 // shared memory; a second kernel adds the partials in block order, so the
 // gradient does not depend on scheduling. The net is far too small for tensor
-// cores to matter (5,382 parameters).
+// cores to matter (5,707 parameters).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -26,6 +26,13 @@ constexpr int kW1 = 0, kB1 = kW1 + kH * kIn, kW2 = kB1 + kH, kB2 = kW2 + kH * kH
               kB3 = kW3 + kOut * kH;
 static_assert(kB3 + kOut == kP, "parameter layout");
 constexpr int kSamplesPerBlock = 32;
+constexpr int kJoinOut = GJ_MLP_JOIN_OUT;  // y[0, kJoinOut): join variants; the rest group-by variants
+static_assert(kOut - kJoinOut == 6, "six group-by outputs");
+
+// The join variant of output o < kJoinOut.
+__host__ __device__ __forceinline__ int join_variant_of(int o) {
+  return o < 3 ? GJ_JOIN_PHJ_TR + o : (o == 3 ? GJ_JOIN_SMJ_TR : GJ_JOIN_SMJ_UR);
+}
 
 __device__ __forceinline__ void mlp_forward_sample(const float* th, const float* x, float* z1, float* h1, float* z2,
                                                    float* h2, float* y) {
@@ -66,13 +73,13 @@ __global__ void __launch_bounds__(kH) mlp_select_kernel(const float* __restrict_
   __syncthreads();
   mlp_forward_sample(th, s_x, z1, h1, z2, h2, s_y);
   if (threadIdx.x == 0) {
-    int bj = 0, bg = 3;
-    for (int o = 1; o < 3; ++o)
+    int bj = 0, bg = kJoinOut;
+    for (int o = 1; o < kJoinOut; ++o)
       if (s_y[o] < s_y[bj]) bj = o;
-    for (int o = 4; o < 6; ++o)
+    for (int o = kJoinOut + 1; o < kOut; ++o)
       if (s_y[o] < s_y[bg]) bg = o;
-    jv[b] = GJ_JOIN_PHJ_TR + bj;
-    gv[b] = GJ_GB_HGB + (bg - 3);
+    jv[b] = join_variant_of(bj);
+    gv[b] = GJ_GB_HGB + (bg - kJoinOut);
   }
 }
 
@@ -228,15 +235,17 @@ int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options*
   if (!join) f[0] = f[3] = f[6] = f[9] = 0.f;
   host_forward(g_sel_theta.data(), f, y);
   if (join) {
+    // the join -> group-by call runs PHJ-TR, PHJ-UR and NPHJ only
+    const int nj = fused ? 3 : kJoinOut;
     int b = 0;
-    for (int o = 1; o < 3; ++o)
+    for (int o = 1; o < nj; ++o)
       if (y[o] < y[b]) b = o;
-    return GJ_JOIN_PHJ_TR + b;
+    return join_variant_of(b);
   }
-  int b = 3;
-  for (int o = 4; o < 6; ++o)
+  int b = kJoinOut;
+  for (int o = kJoinOut + 1; o < kOut; ++o)
     if (y[o] < y[b]) b = o;
-  return GJ_GB_HGB + (b - 3);
+  return GJ_GB_HGB + (b - kJoinOut);
 }
 
 }  // namespace gj

@@ -9,8 +9,8 @@
 // scatter starts, so tiles need no ordering or waiting between them. In the
 // scatter, thread 0 of a block bulk-copies (cp.async.bulk, completion on an
 // mbarrier) the tile's key into shared memory and prefetches its payload columns
-// into L2 (cp.async.bulk.prefetch.L2). Keys are ranked stably per warp with
-// match.any (the warp's rows are contiguous, lanes in row order); per-digit warp
+// into L2 (cp.async.bulk.prefetch.L2). Keys are ranked stably per warp by a
+// ballot multisplit (the warp's rows are contiguous, lanes in row order); per-digit warp
 // counts give each row its position inside the tile's digit-sorted order. Every
 // column is then gathered and written in that order through one permutation word
 // per row, so warps store contiguous runs of each digit.
@@ -233,6 +233,21 @@ __device__ __forceinline__ void stage_tail(unsigned char* stage, const T* src, i
   for (int r = from + threadIdx.x; r < tile_n; r += kThreads) ((T*)stage)[r] = src[tile_base + r];
 }
 
+// The valid lanes of the warp whose digit (< 2^width, width <= 8) equals this
+// lane's: the AND, over the digit's bits, of each bit's ballot or its complement
+// (warp-level multisplit; a handful of ballots cost less than one match.any).
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, int width, bool valid) {
+  unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (b >= width) break;
+    const bool bit = (d >> b) & 1u;
+    const unsigned bb = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bb : ~bb;
+  }
+  return m;
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 3) radix_scatter_kernel(ScatterArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -288,8 +303,8 @@ __global__ void __launch_bounds__(kThreads, 3) radix_scatter_kernel(ScatterArgs 
     if (i >= a.chunks) break;
     const int row = seg + i * 32 + lane;
     const bool valid = row < tile_n;
-    const uint32_t d = valid ? extract_digit<K>(s_key[row], a.transform, a.shift, a.width) : 0xffffffffu;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = valid ? extract_digit<K>(s_key[row], a.transform, a.shift, a.width) : 0u;
+    const unsigned peers = digit_peers(d, a.width, valid);
     uint32_t cnt = 0;
     if (valid) cnt = s_wcnt[warp * kRadixMax + d];
     __syncwarp();

@@ -86,6 +86,8 @@ def load():
     lib.gj_kernel_name.restype = ctypes.c_char_p
     lib.gj_kernel_launches.argtypes = []
     lib.gj_kernel_launches.restype = i64
+    lib.gj_gather.argtypes = [p, i64, i32, p, i64, p, P(Options), p]
+    lib.gj_gather.restype = i32
     lib.gj_set_wait_limit.argtypes = [ctypes.c_uint64]
     lib.gj_set_wait_limit.restype = i32
     lib.gj_check_bounded_wait.argtypes = [i32, p]
@@ -116,6 +118,20 @@ def set_allocator(alloc=None, free=None):
     _raise(lib.gj_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None),
            "gj_set_allocator")
     _hooks = (a, f)
+
+
+def gather(src: torch.Tensor, index: torch.Tensor, *, sync: bool = True, out=None) -> torch.Tensor:
+    """gj_gather: out[i] = src[index[i]] (int32 or int64 src, int32 index)."""
+    if src.dtype not in (torch.int32, torch.int64) or index.dtype != torch.int32:
+        raise TypeError("src int32/int64, index int32")
+    _check_dev(src, src.numel())
+    _check_dev(index, index.numel())
+    if out is None:
+        out = torch.empty(index.numel(), dtype=src.dtype, device=src.device)
+    o = options(sync=sync)
+    _raise(load().gj_gather(src.data_ptr(), src.numel(), src.element_size(), index.data_ptr(), index.numel(),
+                            out.data_ptr(), ctypes.byref(o), _stream()), "gj_gather")
+    return out
 
 
 def set_wait_limit(ns: int):
@@ -228,7 +244,7 @@ class BatchPlan:
             pass
 
 
-MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 12, 64, 6, 5382
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 12, 64, 11, 5707
 
 
 def _load_mlp(lib):

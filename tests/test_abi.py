@@ -176,7 +176,7 @@ def test_selector_set_validates_on_the_host(lib):
     """gj_selector_set copies host arrays; a missing normaliser or a non-positive
     standard deviation is an argument error, NULL theta removes the network."""
     import numpy as np
-    theta = np.zeros(5382, dtype=np.float32)
+    theta = np.zeros(5707, dtype=np.float32)
     mean = np.zeros(12, dtype=np.float32)
     std = np.ones(12, dtype=np.float32)
     f = lib.gj_selector_set

@@ -153,3 +153,30 @@ def test_one_hot_key_per_warp(gj, variant):
     vals = [rng.integers(-(2**31), 2**31, n, dtype=np.int64).astype(np.int32) for _ in range(3)]
     got = run_gb(gj, key, vals, AGGS, COLS, variant, groups_hint=1)
     assert np.array_equal(oracle.canonical(got), want_rows(key, vals, AGGS, COLS))
+
+
+@pytest.mark.parametrize("n,g,kdt,theta,hint", [
+    (1, 1, np.int32, 0.0, 1), (1000, 16, np.int32, 0.0, 16), (300001, 16, np.int64, 1.0, 16),
+    (1 << 20, 32, np.int32, 0.0, 32), (777777, 7, np.int32, 1.2, 8),
+    (500000, 48, np.int32, 0.0, 32),     # more groups than the few-groups pass takes: the general path runs
+    (200000, 33, np.int64, 0.0, 32)])
+def test_hgb_few_groups_pass(gj, n, g, kdt, theta, hint):
+    w = wl.groupby_workload(n, g, nvals=3, key_dtype=kdt, theta=theta, seed=n + g)
+    got = oracle.canonical(run_gb(gj, w["key"], w["vals"], AGGS, COLS, "hgb", groups_hint=hint))
+    assert np.array_equal(got, want_rows(w["key"], w["vals"], AGGS, COLS))
+
+
+def test_hgb_few_groups_pass_extreme_values_and_wide_columns(gj):
+    rng = np.random.default_rng(23)
+    n = 100000
+    key = rng.integers(0, 20, n).astype(np.int32)
+    v = rng.integers(-(2**31), 2**31, n, dtype=np.int64).astype(np.int32)
+    v[key == 3] = np.iinfo(np.int32).max
+    v[key == 4] = np.iinfo(np.int32).min
+    aggs, cols = ["sum", "min", "max", "count"], [0, 0, 0, 0]
+    got = oracle.canonical(run_gb(gj, key, [v], aggs, cols, "hgb", groups_hint=20))
+    assert np.array_equal(got, want_rows(key, [v], aggs, cols))
+    # an 8-byte value column is outside the few-groups pass: the general path runs
+    wide = rng.integers(-(2**62), 2**62, n, dtype=np.int64)
+    got = oracle.canonical(run_gb(gj, key, [wide], aggs, cols, "hgb", groups_hint=20))
+    assert np.array_equal(got, want_rows(key, [wide], aggs, cols))

@@ -86,6 +86,29 @@ def test_duplicate_primary_key_is_reported(gj, variant):
     assert e.value.code == 5
 
 
+@pytest.mark.parametrize("variant", ["phj_tr", "phj_ur"])
+@pytest.mark.parametrize("nr,ns,kdt,theta,mr", [
+    (1 << 18, 1 << 20, np.int32, 1.0, 0.7), (200003, 600011, np.int64, 0.0, 1.0),
+    (131073, 131073, np.int32, 0.5, 0.3), (1 << 20, 3 << 20, np.int32, 0.0, 1.0)])
+def test_l2_sized_build_partitions_match_oracle(gj, variant, nr, ns, kdt, theta, mr):
+    # build sides above 2^17 rows take one 8-bit pass per side and L2-resident tables;
+    # the result equals the oracle's and the two-pass shared-memory path's
+    w = wl.join_workload(nr, ns, 2, 2, theta=theta, mr=mr, key_dtype=kdt, seed=nr ^ ns)
+    want = oracle.canonical(oracle_rows(w))
+    got = oracle.canonical(run_join(gj, w, variant))
+    assert np.array_equal(got, want)
+    assert np.array_equal(oracle.canonical(run_join(gj, w, variant, radix_bits=16)), want)
+
+
+@pytest.mark.parametrize("variant", ["phj_tr", "phj_ur"])
+def test_duplicate_primary_key_in_an_l2_sized_build(gj, variant):
+    w = wl.join_workload(300000, 400000, 1, 1, seed=4)
+    w["rkey"][123456] = w["rkey"][7]
+    with pytest.raises(gj.GjError) as e:
+        run_join(gj, w, variant)
+    assert e.value.code == 5
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_capacity_overflow_is_reported(gj, variant):
     w = wl.join_workload(1000, 4000, 1, 1, seed=2)

@@ -65,8 +65,9 @@ def test_select_is_argmin_per_family(gj):
     theta, x, _, _ = _data(300, 9)
     jv, gv = gj.mlp_select(dev(theta), dev(x))
     y, _ = ref.forward(theta, x)
-    assert np.array_equal(jv.cpu().numpy(), 1 + np.argmin(y[:, :3], 1))
-    assert np.array_equal(gv.cpu().numpy(), 1 + np.argmin(y[:, 3:], 1))
+    join_variants = np.array([1, 2, 3, 5, 6])   # PHJ-TR, PHJ-UR, NPHJ, SMJ-TR, SMJ-UR
+    assert np.array_equal(jv.cpu().numpy(), join_variants[np.argmin(y[:, :5], 1)])
+    assert np.array_equal(gv.cpu().numpy(), 1 + np.argmin(y[:, 5:], 1))
 
 
 def test_training_fits_a_known_function(gj):
@@ -87,7 +88,7 @@ def test_selector_drives_auto(gj):
     import oracle
     th = np.zeros(ref.N_PARAMS, dtype=np.float32)
     p = ref.unpack(th.astype(np.float64))
-    b3 = np.array([1.0, 1.0, -1.0, 1.0, 1.0, -1.0])   # y = b3: argmins NPHJ, PGB
+    b3 = np.array([1.0, 1.0, -1.0, 1.0, 1.0, 1.0, 1.0, -1.0, 1.0, 1.0, 1.0])   # y = b3: argmins NPHJ, PGB
     th = ref.pack({**p, "b3": b3}).astype(np.float32)
     gj.selector_set(th, np.zeros(12), np.ones(12))
     try:
@@ -110,14 +111,16 @@ def test_selector_drives_auto(gj):
 
 @pytest.mark.slow
 def test_trained_selector_beats_the_paper_rules_on_held_out_queries(gj, tmp_path):
-    """Time every variant on a seeded grid (reduced sizes), train on 80 %, and
-    compare regrets on the held-out 20 %."""
+    """Time every variant on a seeded grid of the selector's workload space (|S|
+    capped at 2^21 to bound the test's time), train on 80 %, and check the regret
+    on the held-out 20 %: at most 10 % on average and no worse than the paper's rules."""
     from paper_2312_00720_gb300 import selector
-    pts = selector.grid(200, seed=7, log_s=(14.0, 20.0))
+    pts = selector.grid(400, seed=7, log_s=(16.0, 21.0), log_g=(2.0, 21.0))
     recs = selector.sweep(str(tmp_path / "timings.jsonl"), pts, reps=3)
     train, held = selector.split(recs, 0.8, seed=1)
-    theta, mean, std, losses = selector.train(train, steps=3000)
+    theta, mean, std, losses = selector.train(train, steps=4000)
     ev = selector.evaluate(held, theta, mean, std)
     print(ev)
     assert losses[-1] < losses[0]
+    assert ev["mlp_mean_regret"] <= 0.10
     assert ev["mlp_mean_regret"] <= ev["heuristic_mean_regret"]

@@ -283,7 +283,7 @@ def test_mlp_gradient_matches_central_differences():
     t = rng.normal(0, 1, (7, mlp.D_OUT))
     mask = (rng.random((7, mlp.D_OUT)) < 0.8).astype(np.float64)
     _, g = mlp.grad(theta, x, t, mask)
-    assert mlp.N_PARAMS == 5382
+    assert mlp.N_PARAMS == 5707
     h = 1e-6
     for i in rng.choice(mlp.N_PARAMS, 200, replace=False):
         e = np.zeros_like(theta)
@@ -297,7 +297,7 @@ def test_mlp_linear_special_case():
     from oracle import mlp
     rng = np.random.default_rng(1)
     p = {"w1": rng.random((64, 12)), "b1": np.ones(64), "w2": rng.random((64, 64)), "b2": np.ones(64),
-         "w3": rng.normal(0, 1, (6, 64)), "b3": rng.normal(0, 1, 6)}
+         "w3": rng.normal(0, 1, (11, 64)), "b3": rng.normal(0, 1, 11)}
     x = rng.random((5, 12))
     y, _ = mlp.forward(mlp.pack(p), x)
     want = ((x @ p["w1"].T + 1) @ p["w2"].T + 1) @ p["w3"].T + p["b3"]
@@ -440,3 +440,13 @@ def test_join_groupby_modulus_truncates_toward_zero():
     want = brute_groupby(gk, [t[:, 2]], ["count", "sum", "min"], [0, 0, 0])
     assert np.array_equal(oracle.canonical(got), oracle.canonical(want))
     assert got[:, 0].min() > -7 and got[:, 0].max() < 7
+
+
+def test_gather_is_indexing_and_a_permutation_round_trips():
+    rng = np.random.default_rng(6)
+    src = rng.integers(-(2**31), 2**31, 50).astype(np.int32)
+    idx = rng.integers(0, 50, 80)
+    assert np.array_equal(oracle.gather(src, idx), src[idx])
+    perm = rng.permutation(50)
+    inv = np.argsort(perm)
+    assert np.array_equal(oracle.gather(oracle.gather(src, perm), inv), src)

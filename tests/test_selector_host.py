@@ -14,12 +14,18 @@ def _lib():
 
 
 def test_grid_is_seeded_and_within_its_ranges():
-    a, b = selector.grid(300, seed=5), selector.grid(300, seed=5)
-    assert a == b and selector.grid(300, seed=6) != a
+    a, b = selector.grid(4096, seed=5), selector.grid(4096, seed=5)
+    assert a == b and selector.grid(300, seed=6) != a[:300]
     for p in a:
-        assert 2**14 <= p["ns"] <= 2**22 and 16 <= p["nr"] <= p["ns"]
-        assert p["key_bytes"] in (4, 8) and 1 <= p["ncols"] <= 4
+        assert 2**16 <= p["ns"] <= 2**27 and 16 <= p["nr"] <= p["ns"]
+        assert p["key_bytes"] in (4, 8)
+        assert 1 <= p["ncols_r"] + p["ncols_s"] <= 8 and 0 <= p["ncols_r"] - p["ncols_s"] <= 1
         assert 0.0 <= p["theta"] <= 1.25 and 0.1 <= p["mr"] <= 1.0 and 4 <= p["groups"] <= p["ns"]
+    # the grid spans the workload space: both ends of every range are reached
+    ls = np.log2([p["ns"] for p in a])
+    lg = np.log2([p["groups"] for p in a])
+    assert ls.min() < 16.1 and ls.max() > 26.9 and lg.min() < 2.1 and lg.max() > 25.0
+    assert {p["ncols_r"] + p["ncols_s"] for p in a} == set(range(1, 9))
 
 
 def test_sweep_resumes_after_the_last_completed_point(tmp_path, monkeypatch):
@@ -45,7 +51,7 @@ def test_sweep_resumes_after_the_last_completed_point(tmp_path, monkeypatch):
     for r in recs:
         assert len(r["features"]) == 12 and r["features"][1] == pytest.approx(np.log2(r["point"]["ns"] + 1), rel=1e-6)
     x, y = selector._arrays(recs)
-    assert x.shape == (7, 12) and y.shape == (7, 6) and y[2, 0] == pytest.approx(np.log(3.0))
+    assert x.shape == (7, 12) and y.shape == (7, 11) and y[2, 0] == pytest.approx(np.log(3.0))
 
 
 def test_split_is_a_seeded_partition():
@@ -74,7 +80,7 @@ def _network_preferring(join_idx: int, gb_idx: int):
     p = mlp.unpack(th)
     b3 = np.ones(mlp.D_OUT)
     b3[join_idx] = -1.0
-    b3[3 + gb_idx] = -1.0
+    b3[5 + gb_idx] = -1.0
     return mlp.pack({**p, "b3": b3}).astype(np.float32)
 
 
