@@ -304,18 +304,38 @@ def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6784.5):
     return out
 
 
+def _seq_variants(gj, ws):
+    """How many of the instances each join variant runs under the paper's rules."""
+    inv = {v: k for k, v in gj.JOIN.items()}
+    out = {}
+    for w in ws:
+        j, _ = gj.auto_variants(len(w["rkey"]), len(w["skey"]), 4, 2, 2, 4, -1.0, -1.0, 0, selector="heuristic",
+                                fused=True)
+        out[inv[j]] = out.get(inv[j], 0) + 1
+    return out
+
+
 def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):
-    """512 join + group-by instances: one persistent graph launch vs 512 sequential gj_join_groupby calls."""
+    """512 join + group-by instances: the batched plan with each query's variant chosen
+    by the trained network (the cost model if the package ships none) vs 512 sequential
+    gj_join_groupby calls whose AUTO follows the paper's rules."""
     import torch
+    from paper_2312_00720_gb300 import selector as sel
     ws = wl.batch_workload(512, seed=7)
     d = lambda a: torch.from_numpy(a).cuda()
     aggs = ["count", "sum", "sum", "sum"]
     refs = [(1, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)]
     qs = [(d(w["rkey"]), [d(c) for c in w["rcols"]], d(w["skey"]), [d(c) for c in w["scols"]],
            (0, 0, w["modulus"]), aggs, refs) for w in ws]
+    learned = sel.install_trained()
     t0 = time.perf_counter()
-    plan = gj.BatchPlan(qs)
+    plan = gj.BatchPlan(qs, selector="mlp" if learned else "cost")
     tune_s = time.perf_counter() - t0
+    gj.selector_set(None, None, None)
+    inv = {v: k for k, v in gj.JOIN.items()}
+    batched_variants = {}
+    for v in plan.variants():
+        batched_variants[inv[v]] = batched_variants.get(inv[v], 0) + 1
     batched = _event_ms(plan.launch, steps)
     res = plan.results()
     assert gj.device_status() == 0
@@ -323,7 +343,7 @@ def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):
 
     def sequential():
         for q in qs:
-            gj.join_groupby(*q, variant="auto", sync=False, capacity=2 * q[4][2] - 1)
+            gj.join_groupby(*q, variant="auto", selector="heuristic", sync=False, capacity=2 * q[4][2] - 1)
 
     seq = _event_ms(sequential, max(1, steps // 2))
     rows = sum(len(w["rkey"]) + len(w["skey"]) for w in ws)
@@ -345,6 +365,10 @@ def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):
             # minimal bytes: every input row (key + 2 payloads) read once
             "batched_min_bytes_frac": rows * 12 / (batched * 1e-3) / 1e9 / peak,
             "tuned_config": {"build_rows": cfg[0], "probe_rows": cfg[1], "lookahead": cfg[2], "blocks_per_sm": cfg[3]},
+            "batched_selector": "trained network (selector_gb300.npz)" if learned else "cost model",
+            "batched_variants": batched_variants,
+            "sequential_selector": "the paper's rules (Sec. 7)",
+            "sequential_variants": _seq_variants(gj, ws),
             "tune_and_capture_s": tune_s}
 
 
@@ -441,6 +465,60 @@ def groupby_case(spec: str):
     print(json.dumps({"groupby_case": {"n": 1 << lgn, "ids": 1 << lgg, "groups": groups}}))
 
 
+def kernel_families():
+    """One launch of each kernel family on small cases (inputs larger than L2, a few
+    GB on the device at most), synchronised, for profiler captures; no timing.
+    Joins |R| = 2^22, |S| = 2^24 with 4 + 4 int32 payloads (PHJ-TR, PHJ-UR, NPHJ,
+    SMJ-TR); NPHJ-MN on 2^22 x 2^22 rows over 2^21 keys; the one-query fused
+    join -> group-by (NPHJ and PHJ-TR plans); group-by of 2^24 rows with 10
+    aggregates (HGB over 2^12 ids, PGB and SGB over 2^20); a 64-instance batch;
+    one selector training step (loss + gradient, Adam)."""
+    import numpy as np
+    import torch
+
+    from paper_2312_00720_gb300 import gj, selector
+    from paper_2312_00720_gb300 import workloads as wl
+
+    gj.load()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    w = wl.join_workload(1 << 22, 1 << 24, 4, 4, seed=1)
+    rk, rc, sk, sc = d(w["rkey"]), [d(c) for c in w["rcols"]], d(w["skey"]), [d(c) for c in w["scols"]]
+    for v in ("phj_tr", "phj_ur", "nphj", "smj_tr"):
+        gj.join(rk, rc, sk, sc, variant=v)
+    del rk, rc, sk, sc
+    wm = wl.mn_join_workload(1 << 22, 1 << 22, 1 << 21, 2, 2, seed=2)
+    gj.join(d(wm["rkey"]), [d(c) for c in wm["rcols"]], d(wm["skey"]), [d(c) for c in wm["scols"]],
+            variant="nphj_mn", capacity=int(1.1 * (1 << 23)))
+    wq = wl.join_groupby_workload()
+    qargs = (d(wq["rkey"]), [d(wq["rcols"][0])], d(wq["skey"]), [d(wq["scols"][0])], (0, 0, 1024),
+             ["sum", "count"], [(1, 0, 0), (1, 0, 0)])
+    for v in ("nphj", "phj_tr"):
+        gj.join_groupby(*qargs, variant=v)
+    aggs = ["count"] + ["sum", "min", "max"] * 3
+    cols = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
+    for lg, v in ((12, "hgb"), (20, "pgb"), (20, "sgb")):
+        g = wl.groupby_workload(1 << 24, 1 << lg, nvals=3, seed=7)
+        gj.groupby(d(g["key"]), [d(x) for x in g["vals"]], aggs, cols, variant=v, groups_hint=1 << lg)
+    ws = wl.batch_workload(64, seed=7)
+    qs = [(d(b["rkey"]), [d(c) for c in b["rcols"]], d(b["skey"]), [d(c) for c in b["scols"]], (0, 0, b["modulus"]),
+           ["count", "sum", "sum", "sum"], [(1, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)]) for b in ws]
+    plan = gj.BatchPlan(qs, config=(8192, 8192, 4, 3))
+    plan.launch()
+    torch.cuda.synchronize()
+    plan.close()
+    th = torch.from_numpy(selector.init_params(0)).cuda()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    x = torch.randn(512, 12, device="cuda", generator=gen)
+    t = torch.randn(512, 11, device="cuda", generator=gen)
+    loss, grad = gj.mlp_loss_grad(th, x, t, torch.ones(512, 11, device="cuda"))
+    gj.mlp_adam_step(th, grad, torch.zeros_like(th), torch.zeros_like(th), 1, lr=1e-3)
+    torch.cuda.synchronize()
+    if gj.device_status() != 0:
+        raise RuntimeError("device error in the kernel families")
+    print(json.dumps({"kernel_families": "done"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,9 +533,14 @@ def main():
     ap.add_argument("--groupby-case", default=None, metavar="LOG2N,LOG2G,VARIANT[,VARIANT..]",
                     help="run each group-by variant once on 2^LOG2N rows over 2^LOG2G ids and exit "
                          "(the small case the group-by kernel captures are taken on)")
+    ap.add_argument("--kernel-families", action="store_true",
+                    help="run one launch of each kernel family on small cases and exit (profiler captures)")
     args = ap.parse_args()
     if args.groupby_case:
         groupby_case(args.groupby_case)
+        return
+    if args.kernel_families:
+        kernel_families()
         return
     global NR, NS, MIN_BYTES
     NR, NS = NR >> args.scale, NS >> args.scale

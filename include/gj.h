@@ -105,7 +105,10 @@ typedef enum {
                        stream once to read g */
 } gj_groupby_variant;
 
-typedef enum { GJ_SELECT_HEURISTIC = 0, GJ_SELECT_MLP = 1 } gj_selector_mode;
+/* How AUTO picks a variant: the paper's rules (Sec. 7, Fig. groupby-dt), the
+ * trained network (Sec. 6's learned selection; the cost model while no network
+ * is installed), or the GB300-calibrated cost model (gj_cost_estimate). */
+typedef enum { GJ_SELECT_HEURISTIC = 0, GJ_SELECT_MLP = 1, GJ_SELECT_COST = 2 } gj_selector_mode;
 
 typedef struct {
   int32_t join_variant;     /* gj_join_variant */
@@ -122,7 +125,7 @@ typedef struct {
                                PGB's partition count, and is a selector feature */
 } gj_options;
 
-/* Fills *opt with the defaults (AUTO variants, heuristic selector, sync = 0). */
+/* Fills *opt with the defaults (AUTO variants, the cost-model selector, sync = 0). */
 void gj_options_default(gj_options* opt);
 
 /* Human-readable name of a status code; never NULL. */
@@ -239,9 +242,9 @@ gj_status gj_join_groupby(const gj_table* R, const gj_table* S, gj_colref group_
  * launch is captured once in a CUDA graph and replayed. The paper has no
  * batched mode; each query computes exactly what gj_join_groupby computes.
  *
- * Restrictions of the batched path: int32 keys; group_key.modulus in
+ * Restrictions of the persistent kernel: int32 keys; group_key.modulus in
  * [1, 2^20] (groups are the residues, read as dense slots); at most
- * GJ_BATCH_MAX_AGGS aggregates per query. Column and output pointers are
+ * GJ_BATCH_MAX_AGGS aggregates per query (a limit of every query). Column and output pointers are
  * device memory that must stay valid and at the same address for the life of
  * the plan; every launch recomputes all outputs from the current input
  * contents. */
@@ -273,15 +276,25 @@ typedef struct {
   int32_t blocks_per_sm;
 } gj_batch_config;
 
-/* Validates the queries, uploads the task queue, allocates the workspace,
+/* Validates the queries and chooses each one's join variant: opt->join_variant
+ * for all of them, or with AUTO the choice opt->selector makes for that query
+ * as gj_join_groupby would (PHJ-TR, PHJ-UR or NPHJ; opt's hints apply to every
+ * query; opt NULL = defaults). Queries that run NPHJ within the restrictions
+ * above go to the persistent kernel; the others (another variant, int64 keys,
+ * a modulus outside [1, 2^20]) run one at a time after it through the
+ * gj_join_groupby path. Then uploads the task queue, allocates the workspace,
  * runs the autotuner for the zero fields of *cfg (cfg may be NULL: all
  * tuned; the tuner times each candidate on this batch and keeps the fastest;
  * results are cached per device and batch shape), and captures the chosen
  * configuration in a CUDA graph. `stream` is used for tuning and set-up. */
-gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_config* cfg,
+gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_config* cfg, const gj_options* opt,
                           gj_batch_plan** plan, void* stream);
-/* Replays the captured graph on `stream`: all nq queries, asynchronously. */
+/* Replays the captured graph on `stream`, then runs the queries that run alone:
+ * all nq queries, asynchronously (the one-at-a-time queries allocate and free
+ * their scratch through the allocator as gj_join_groupby does). */
 gj_status gj_batch_launch(gj_batch_plan* plan, void* stream);
+/* variants[nq]: the gj_join_variant each query of the plan runs. */
+gj_status gj_batch_get_variants(const gj_batch_plan* plan, int32_t* variants);
 /* The configuration the plan runs with. */
 gj_status gj_batch_get_config(const gj_batch_plan* plan, gj_batch_config* cfg);
 /* Frees the plan, its graph and workspace (synchronises the device). */
@@ -327,7 +340,7 @@ gj_status gj_mlp_select(const float* theta, const float* x, int32_t n, int32_t* 
  * PHJ-TR, PHJ-UR and NPHJ only, takes the argmin of y0..y2). host_theta: GJ_MLP_PARAMS floats (host);
  * mean / stdev: GJ_MLP_IN floats (host) normalising the raw features
  * (x - mean) / stdev. Passing NULL theta removes the network, and AUTO falls
- * back to the paper's rules. The raw features of a query are
+ * back to the cost model (gj_cost_estimate). The raw features of a query are
  *   0 log2(|R|+1)  1 log2(|S|+1)  2 key bytes  3 R payload columns
  *   4 S payload columns  5 Zipf factor  6 match ratio  7 log2(groups+1)
  *   8 aggregates  9 log2((|R|+1)/(|S|+1))  10 payload bytes per S row
@@ -353,6 +366,49 @@ gj_status gj_heuristic_choose(const gj_table* R, const gj_table* S, int32_t nagg
  * follows opt->selector as the operators do. Either output pointer may be NULL. */
 gj_status gj_auto_variants(const gj_table* R, const gj_table* S, int32_t nagg, const int32_t* ops,
                            const gj_options* opt, int32_t fused, int32_t* join_variant, int32_t* gb_variant);
+/* ---- Cost-model selection (Sec. 4.1.1, 4.1.3, 4.1.4, 4.4) ------------------
+ * The paper's bandwidth models carried over to every variant of this library:
+ * a variant's cost is the bytes it moves in units of sequential global-memory
+ * bytes (cost / B_G is a time). Unclustered accesses count B_G / B_R times their
+ * bytes (M1; B_R measured with the clustered-vs-unclustered gather of Table
+ * gather-profile, gj_gather), or B_G / B_L2 times when the structure they go to
+ * fits in l2_bytes; every kernel launch and host synchronisation adds a fixed
+ * cost; the partition-based group-by pays for its hottest partition (share
+ * 1 / H(g, z) of the rows under Zipf factor z) on one SM. Fields <= 0 that
+ * name device figures (l2_bytes, smem_bytes, num_sms) are read from the current
+ * device, or take GB300's when there is none. */
+typedef struct {
+  double bg_over_br;    /* B_G / B_R: unclustered-access slowdown beyond L2 (>= 1) */
+  double bg_over_bl2;   /* B_G / B_L2: unclustered-access slowdown inside l2_bytes (>= 1) */
+  double l2_bytes;      /* footprint that counts as L2-resident; 0 = half the device's L2 */
+  double smem_bytes;    /* shared memory per block for HGB's aggregates; 0 = the device's opt-in maximum */
+  double launch_bytes;  /* fixed cost of one kernel launch, in bytes at B_G */
+  double sync_bytes;    /* fixed cost of one host synchronisation inside a call */
+  double hot_row_bytes; /* bytes of work per row of the hottest PGB partition */
+  int32_t num_sms;      /* 0 = the device's */
+  int32_t reserved;
+} gj_cost_params;
+
+/* GB300 defaults: B_G / B_R = 27.5 (measured: unclustered gathers 9.82x slower
+ * than clustered ones over 2^27 int32, and the paper's reading of that gap,
+ * B_G / B_R = 3 x gap - 2), B_G / B_L2 = 27.5 / 4.5 (the paper's B_L2 = 4.5 B_G),
+ * launch 2e7 and synchronisation 6e7 bytes (about 3 and 9 us at 6.8 TB/s),
+ * 20 bytes per hot-partition row. */
+void gj_cost_params_default(gj_cost_params* p);
+/* Installs the parameters used by GJ_SELECT_COST (and by GJ_SELECT_MLP without
+ * a network) in this process; NULL restores the defaults. Ratios below 1 or
+ * negative sizes give GJ_ERR_INVALID_ARG. */
+gj_status gj_set_cost_params(const gj_cost_params* p);
+/* The model's costs (bytes at B_G) under the installed parameters, host only:
+ * join_cost[5] for PHJ-TR, PHJ-UR, NPHJ, SMJ-TR, SMJ-UR of R join S (R needed),
+ * gb_cost[6] for HGB, SGB, PGB, SGB-UR, PGB-UR, SGB-DE of a group-by of S with
+ * nagg aggregates ops[] (ops NULL: SUMs) over all of S's columns. Hints in *opt
+ * stand in for the match ratio (unknown: 1), Zipf factor (unknown: 0) and group
+ * count (unknown: |S|). Either output may be NULL; column pointers are not read.
+ * GJ_SELECT_COST picks the argmin (of the first three for gj_join_groupby). */
+gj_status gj_cost_estimate(const gj_table* R, const gj_table* S, int32_t nagg, const int32_t* ops,
+                           const gj_options* opt, double* join_cost, double* gb_cost);
+
 /* Writes the 12 raw features of a query into out[12] (host). Either table may be
  * NULL when only one operator is chosen. */
 gj_status gj_query_features(const gj_table* R, const gj_table* S, int32_t nagg, const gj_options* opt, float* out);

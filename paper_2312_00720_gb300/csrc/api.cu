@@ -244,7 +244,7 @@ void gj_options_default(gj_options* opt) {
   memset(opt, 0, sizeof(*opt));
   opt->join_variant = GJ_JOIN_AUTO;
   opt->groupby_variant = GJ_GB_AUTO;
-  opt->selector = GJ_SELECT_HEURISTIC;
+  opt->selector = GJ_SELECT_COST;
   opt->zipf_hint = -1.0f;
   opt->match_ratio_hint = -1.0f;
 }

@@ -258,6 +258,13 @@ struct gj_batch_plan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int* d_status = nullptr;
+  // per query of the request: the join variant it runs; queries not run by the
+  // persistent kernel go through the one-query path after it, with these options
+  int nq_total = 0;
+  std::vector<int32_t> variant;
+  std::vector<int> solo;
+  std::vector<gj_query> queries;
+  gj_options solo_opt{};
 };
 
 namespace gj {
@@ -272,18 +279,18 @@ bool valid_ref(const gj_query& q, const gj_colref& r) {
   return r.col >= -1 && r.col < t.ncols && r.modulus >= 0;
 }
 
+// Checks every query must pass; batchable() adds the persistent kernel's limits.
 gj_status check_query(const gj_query& q) {
   for (const gj_table* t : {&q.R, &q.S}) {
-    if (t->key_type != GJ_I32) return GJ_ERR_UNSUPPORTED;
+    if (t->key_type != GJ_I32 && t->key_type != GJ_I64) return GJ_ERR_INVALID_ARG;
     if (t->ncols < 0 || t->ncols > GJ_MAX_COLS || t->n < 0) return GJ_ERR_INVALID_ARG;
-    if (t->n > kMaxRows) return GJ_ERR_UNSUPPORTED;
     if (t->n > 0 && !t->key) return GJ_ERR_INVALID_ARG;
     for (int c = 0; c < t->ncols; ++c)
       if ((t->col_type[c] != GJ_I32 && t->col_type[c] != GJ_I64) || (t->n > 0 && !t->cols[c]))
         return GJ_ERR_INVALID_ARG;
   }
+  if (q.R.key_type != q.S.key_type) return GJ_ERR_INVALID_ARG;
   if (!valid_ref(q, q.group_key)) return GJ_ERR_INVALID_ARG;
-  if (q.group_key.modulus < 1 || q.group_key.modulus > (1 << 20)) return GJ_ERR_UNSUPPORTED;
   if (q.nagg < 1 || q.nagg > GJ_BATCH_MAX_AGGS) return GJ_ERR_INVALID_ARG;
   for (int j = 0; j < q.nagg; ++j) {
     if (q.ops[j] < GJ_AGG_SUM || q.ops[j] > GJ_AGG_MAX) return GJ_ERR_INVALID_ARG;
@@ -292,6 +299,11 @@ gj_status check_query(const gj_query& q) {
   }
   if (q.capacity < 0 || !q.d_ngroups || (q.capacity > 0 && !q.out_keys)) return GJ_ERR_INVALID_ARG;
   return GJ_OK;
+}
+
+bool batchable(const gj_query& q) {
+  return q.R.key_type == GJ_I32 && q.R.n <= kMaxRows && q.S.n <= kMaxRows && q.group_key.modulus >= 1 &&
+         q.group_key.modulus <= (1 << 20);
 }
 
 BRef make_ref(const gj_query& q, const gj_colref& r) {
@@ -414,9 +426,16 @@ float time_plan(gj_batch_plan* P, cudaStream_t s, int reps) {
 
 extern "C" {
 
-gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_config* cfg_in, gj_batch_plan** out,
-                          void* stream) {
+gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_config* cfg_in, const gj_options* opt,
+                          gj_batch_plan** out, void* stream) {
   if (!out || nq < 0 || (nq > 0 && !queries)) return GJ_ERR_INVALID_ARG;
+  gj_options o;
+  gj_options_default(&o);
+  if (opt) o = *opt;
+  if (o.join_variant != GJ_JOIN_AUTO && o.join_variant != GJ_JOIN_PHJ_TR && o.join_variant != GJ_JOIN_PHJ_UR &&
+      o.join_variant != GJ_JOIN_NPHJ)
+    return GJ_ERR_INVALID_ARG;
+  if (o.radix_bits < 0 || o.radix_bits > 16 || o.bits_per_pass < 0 || o.bits_per_pass > 8) return GJ_ERR_INVALID_ARG;
   for (int q = 0; q < nq; ++q) {
     gj_status st = check_query(queries[q]);
     if (st != GJ_OK) return st;
@@ -431,8 +450,11 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
   auto* P = new gj_batch_plan();
   P->device = ctx.device;
   P->num_sms = ctx.num_sms;
-  P->nq = nq;
+  P->nq_total = nq;
   P->d_status = ctx.d_status;
+  P->queries.assign(queries, queries + nq);
+  P->solo_opt = o;
+  P->solo_opt.sync = 0;
   auto fail = [&](gj_status e) {
     gj_batch_destroy(P);
     return e;
@@ -441,6 +463,15 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
   bool any_smem = false;
   for (int q = 0; q < nq; ++q) {
     const gj_query& Q = queries[q];
+    // the variant this query runs (Sec. 7's choice made per query); the persistent
+    // kernel runs the non-partitioned join, every other choice and every query
+    // outside its limits runs alone after it
+    const int v = resolve_join_variant(&Q.R, &Q.S, Q.nagg, &o, true);
+    P->variant.push_back(v);
+    if (v != GJ_JOIN_NPHJ || !batchable(Q)) {
+      P->solo.push_back(q);
+      continue;
+    }
     BInst I{};
     I.rkey = (const int32_t*)Q.R.key;
     I.skey = (const int32_t*)Q.S.key;
@@ -480,6 +511,12 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
     sum_s += I.ns;
     sum_slots += I.nslots;
   }
+  P->nq = (int)P->h_insts.size();
+  if (P->nq == 0) {  // nothing for the persistent kernel
+    *out = P;
+    return GJ_OK;
+  }
+  nq = P->nq;
   P->dyn = any_smem ? kSmemAgg : 0;
   if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAgg) != cudaSuccess)
     return fail(GJ_ERR_CUDA);
@@ -532,12 +569,29 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
 }
 
 gj_status gj_batch_launch(gj_batch_plan* P, void* stream) {
-  if (!P || !P->exec) return GJ_ERR_INVALID_ARG;
+  if (!P || (P->nq > 0 && !P->exec)) return GJ_ERR_INVALID_ARG;
   Ctx ctx;
   gj_status st = make_ctx(stream, &ctx);
   if (st != GJ_OK) return st;
-  LaunchScope ls(ctx, KK_BATCH);
-  return cuda_check(cudaGraphLaunch(P->exec, (cudaStream_t)stream));
+  if (P->exec) {
+    LaunchScope ls(ctx, KK_BATCH);
+    if ((st = cuda_check(cudaGraphLaunch(P->exec, (cudaStream_t)stream))) != GJ_OK) return st;
+  }
+  for (int q : P->solo) {
+    const gj_query& Q = P->queries[q];
+    gj_options o = P->solo_opt;
+    o.join_variant = P->variant[q];
+    if ((st = join_groupby_run(ctx, &Q.R, &Q.S, Q.group_key, Q.nagg, Q.ops, Q.agg_cols, &o, Q.out_keys, Q.out_aggs,
+                               Q.capacity, Q.d_ngroups)) != GJ_OK)
+      return st;
+  }
+  return GJ_OK;
+}
+
+gj_status gj_batch_get_variants(const gj_batch_plan* P, int32_t* variants) {
+  if (!P || (P->nq_total > 0 && !variants)) return GJ_ERR_INVALID_ARG;
+  std::copy(P->variant.begin(), P->variant.end(), variants);
+  return GJ_OK;
 }
 
 gj_status gj_batch_get_config(const gj_batch_plan* P, gj_batch_config* cfg) {

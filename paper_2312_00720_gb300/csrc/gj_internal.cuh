@@ -467,9 +467,15 @@ int choose_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, con
 void query_features(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, float* f);
 int mlp_choose(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool join, bool fused);
 
+// The GB300-calibrated cost model's choice (argmin of gj_cost_estimate; `fused`
+// as for mlp_choose).
+int cost_join_variant(const gj_table* R, const gj_table* S, const gj_options* opt, bool fused);
+int cost_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt);
+
 // The variants an AUTO request runs: the trained network's choice when
-// options.selector is GJ_SELECT_MLP and a network is installed, else the paper's
-// rules; an explicit variant is returned unchanged.
+// options.selector is GJ_SELECT_MLP and a network is installed, the paper's rules
+// under GJ_SELECT_HEURISTIC, else the cost model; an explicit variant is returned
+// unchanged.
 int resolve_join_variant(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool fused);
 int resolve_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, const gj_options* opt,
                             int smem_budget);

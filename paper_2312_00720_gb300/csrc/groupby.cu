@@ -106,7 +106,7 @@ __device__ __forceinline__ int32_t hgb_find(const HEntry<K>* __restrict__ ht, ui
 // so that a key repeated across the block's rows reaches the global table once per
 // block. 4-byte keys are tagged with bit 32 (empty = 0); 8-byte keys are stored as
 // they are (empty = INT64_MIN, a key of that value is simply never cached).
-constexpr int kSeenSlots = 16384;  // 128 KB: one 1024-thread block per SM
+constexpr int kSeenSlots = 16384;  // 192 KB with the rows: one 1024-thread block per SM
 constexpr int kSeenProbes = 4;
 template <typename K>
 __device__ __forceinline__ unsigned long long seen_tag(K k) {
@@ -117,14 +117,20 @@ __device__ __forceinline__ unsigned long long seen_empty() {
   return sizeof(K) == 4 ? 0ull : 0x8000000000000000ull;
 }
 
-// Stage 1: build the dictionary. Writes nothing per row.
+// Stage 1: build the dictionary. Writes nothing per row. A block first only
+// collects its distinct keys in the shared-memory set (with one row holding each,
+// which the global insert needs); keys that do not fit the set go to the global
+// table at once. At the end all threads of the block insert the collected keys
+// together, so the global round trips run in full warps rather than one diverged
+// lane at a time.
 template <typename K>
 __global__ void __launch_bounds__(1024, 1) hgb_dict_kernel(const K* __restrict__ key, int64_t n, HEntry<K>* ht,
                                                        uint64_t mask, unsigned long long* ngroups,
                                                        K* __restrict__ out_keys, int64_t cap, const int* gate,
                                                        int* err) {
   if (gate && *gate == 0) return;  // the few-groups pass has produced the result
-  extern __shared__ unsigned long long s_seen[];  // kSeenSlots entries
+  extern __shared__ unsigned long long s_seen[];  // kSeenSlots tags, then kSeenSlots rows (int32)
+  int32_t* s_row = reinterpret_cast<int32_t*>(s_seen + kSeenSlots);
   __shared__ int s_fill;  // keys cached; new keys stop being cached at half load
   const unsigned long long empty = seen_empty<K>();
   for (int j = threadIdx.x; j < kSeenSlots; j += blockDim.x) s_seen[j] = empty;
@@ -146,26 +152,35 @@ __global__ void __launch_bounds__(1024, 1) hgb_dict_kernel(const K* __restrict__
       const unsigned long long tag = seen_tag<K>(kk[u]);
       bool handled = false;
       if (tag != empty) {
-        uint32_t s = (uint32_t)KeyTraits<K>::hash64(kk[u]) & (kSeenSlots - 1);
+        uint32_t sl = (uint32_t)KeyTraits<K>::hash64(kk[u]) & (kSeenSlots - 1);
         for (int p = 0; p < kSeenProbes; ++p) {
-          unsigned long long v = s_seen[s];
+          unsigned long long v = s_seen[sl];
           if (v == empty) {
             if (*(volatile int*)&s_fill >= kSeenSlots / 2) break;  // full enough: look up only
-            v = atomicCAS(&s_seen[s], empty, tag);
+            v = atomicCAS(&s_seen[sl], empty, tag);
             if (v == empty) {
+              s_row[sl] = (int32_t)i;  // inserted into the global table at the end
               atomicAdd(&s_fill, 1);
-              break;  // this row inserts the key on the block's behalf
+              handled = true;
+              break;
             }
           }
           if (v == tag) {
-            handled = true;  // another row of the block has inserted or found it
+            handled = true;  // collected already
             break;
           }
-          s = (s + 1) & (kSeenSlots - 1);
+          sl = (sl + 1) & (kSeenSlots - 1);
         }
       }
       if (!handled) hgb_insert<K>(key, ht, mask, kk[u], i, ngroups, out_keys, cap, err);
     }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < kSeenSlots; j += blockDim.x) {
+    const unsigned long long tag = s_seen[j];
+    if (tag == empty) continue;
+    const K k = sizeof(K) == 4 ? (K)(int32_t)(uint32_t)tag : (K)(int64_t)tag;
+    hgb_insert<K>(key, ht, mask, k, s_row[j], ngroups, out_keys, cap, err);
   }
 }
 
@@ -1530,7 +1545,7 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     LaunchScope ls(ctx, KK_HGB_GROUP_ID);
     // one block per SM with its key cache
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms));
-    const int cache_bytes = kSeenSlots * (int)sizeof(unsigned long long);
+    const int cache_bytes = kSeenSlots * (int)(sizeof(unsigned long long) + sizeof(int32_t));
     if ((st = ensure_smem_attr(ctx, (const void*)hgb_dict_kernel<K>, cache_bytes)) != GJ_OK) return st;
     hgb_dict_kernel<K><<<blocks, 1024, cache_bytes, s>>>((const K*)in->key, n, ht, slots - 1,
                                                          (unsigned long long*)d_ngroups, (K*)out_keys, cap, gate,
@@ -1749,7 +1764,9 @@ int resolve_groupby_variant(const gj_table* in, int nagg, const int32_t* ops, co
                             int smem_budget) {
   int variant = opt->groupby_variant;
   if (variant == GJ_GB_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(nullptr, in, nagg, opt, false, false);
-  if (variant == GJ_GB_AUTO) variant = choose_groupby_variant(in, nagg, ops, opt, smem_budget);
+  if (variant == GJ_GB_AUTO)
+    variant = opt->selector == GJ_SELECT_HEURISTIC ? choose_groupby_variant(in, nagg, ops, opt, smem_budget)
+                                                   : cost_groupby_variant(in, nagg, ops, opt);
   return variant;
 }
 

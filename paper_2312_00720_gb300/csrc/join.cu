@@ -689,26 +689,36 @@ __global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rke
     __syncthreads();
     if (c0 >= nr) return;
     const int64_t c1 = min64(nr, c0 + kL2BuildChunk);
-    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
-      const K k = rkey[i];
-      const uint64_t h = KeyTraits<K>::hash64(k);
-      const int P = (int)(h & (kL2Parts - 1));
-      const int64_t base = toff[P];
-      const uint64_t msk = (uint64_t)(toff[P + 1] - base) - 1;
-      uint64_t sl = (h >> kL2Bits) & msk;
-      if constexpr (sizeof(K) == 4) {
+    if constexpr (sizeof(K) == 4) {
+      // one row per thread in flight (batching several rows' compare-and-swaps
+      // per thread made the build 1.7x slower)
+      for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const K k = rkey[i];
+        const uint64_t h = KeyTraits<K>::hash64(k);
+        const int P = (int)(h & (kL2Parts - 1));
+        const int64_t base = toff[P];
+        const uint64_t msk = (uint64_t)(toff[P + 1] - base) - 1;
+        uint64_t sl = (h >> kL2Bits) & msk;
         auto* t = reinterpret_cast<unsigned long long*>(table) + base;
         const unsigned long long w = L2Slot<int32_t>::make((int32_t)k, i);
         for (uint64_t probe = 0; probe <= msk; ++probe) {
           const unsigned long long prev = atomicCAS(&t[sl], 0ull, w);
           if (prev == 0ull) break;
-          if ((int32_t)(uint32_t)prev == (int32_t)k) {
+          if ((uint32_t)prev == (uint32_t)w) {
             set_status(err, GJ_ERR_DUPLICATE_KEY);
             break;
           }
           sl = (sl + 1) & msk;
         }
-      } else {
+      }
+    } else {
+      for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) {
+        const K k = rkey[i];
+        const uint64_t h = KeyTraits<K>::hash64(k);
+        const int P = (int)(h & (kL2Parts - 1));
+        const int64_t base = toff[P];
+        const uint64_t msk = (uint64_t)(toff[P + 1] - base) - 1;
+        uint64_t sl = (h >> kL2Bits) & msk;
         int32_t* t = table + base;
         for (uint64_t probe = 0; probe <= msk; ++probe) {
           const int prev = atomicCAS(&t[sl], 0, (int)(i + 1));
@@ -724,25 +734,26 @@ __global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rke
   }
 }
 
-// The R' row of key k in the table of its partition, or -1.
+// The R' row of key k in the table of its partition, or -1, given the word w
+// already read at its first slot sl.
 template <typename K>
-__device__ __forceinline__ int32_t l2_find(const K* __restrict__ rkey, const int32_t* __restrict__ table,
-                                           int64_t base, uint64_t msk, uint64_t sl, K k) {
+__device__ __forceinline__ int32_t l2_resolve(const K* __restrict__ rkey, const int32_t* __restrict__ table,
+                                              int64_t base, uint64_t msk, uint64_t sl, typename L2Slot<K>::W w, K k) {
   if constexpr (sizeof(K) == 4) {
     const auto* t = reinterpret_cast<const unsigned long long*>(table) + base;
     for (uint64_t probe = 0; probe <= msk; ++probe) {
-      const unsigned long long w = __ldg(t + sl);
       if (w == 0ull) return -1;
       if ((int32_t)(uint32_t)w == (int32_t)k) return (int32_t)(w >> 32) - 1;
       sl = (sl + 1) & msk;
+      w = __ldg(t + sl);
     }
   } else {
     const int32_t* t = table + base;
     for (uint64_t probe = 0; probe <= msk; ++probe) {
-      const int v = __ldg(t + sl);
-      if (v == 0) return -1;
-      if (__ldg(rkey + v - 1) == k) return v - 1;
+      if (w == 0) return -1;
+      if (__ldg(rkey + w - 1) == k) return w - 1;
       sl = (sl + 1) & msk;
+      w = __ldg(t + sl);
     }
   }
   return -1;
@@ -777,15 +788,27 @@ __global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __re
       const int r = r0 + q * kThreads + t;
       k[q] = r < un ? __ldcs(skey + u0 + r) : K(0);
     }
+    // the first slot of every row of the batch is read before any is resolved, so
+    // the batch's L2 round trips overlap; a collision continues on its own
+    int64_t base[kLook];
+    uint64_t msk[kLook], sl[kLook];
+    typename L2Slot<K>::W w[kLook];
+#pragma unroll
+    for (int q = 0; q < kLook; ++q) {
+      const uint64_t h = KeyTraits<K>::hash64(k[q]);
+      const int P = (int)(h & (kL2Parts - 1));
+      base[q] = s_toff[P];  // in entries
+      msk[q] = (uint64_t)(s_toff[P + 1] - s_toff[P]) - 1;
+      sl[q] = (h >> kL2Bits) & msk[q];
+      const bool in = r0 + q * kThreads + t < un;
+      w[q] = in ? __ldg(reinterpret_cast<const typename L2Slot<K>::W*>(table) + base[q] + sl[q])
+                : typename L2Slot<K>::W(0);
+    }
 #pragma unroll
     for (int q = 0; q < kLook; ++q) {
       const int r = r0 + q * kThreads + t;
       if (r >= un) continue;
-      const uint64_t h = KeyTraits<K>::hash64(k[q]);
-      const int P = (int)(h & (kL2Parts - 1));
-      const int64_t base = s_toff[P];  // in entries
-      const uint64_t msk = (uint64_t)(s_toff[P + 1] - s_toff[P]) - 1;
-      s_midx[r] = l2_find<K>(rkey, table, base, msk, (h >> kL2Bits) & msk, k[q]);
+      s_midx[r] = l2_resolve<K>(rkey, table, base[q], msk[q], sl[q], w[q], k[q]);
     }
   }
   __syncthreads();
@@ -1334,6 +1357,45 @@ __global__ void __launch_bounds__(kThreads) group_emit_kernel(GroupSink G, int64
   if (overflow) set_status(err, GJ_ERR_CAPACITY);
 }
 
+// The tables of the L2-sized build partitions of R' (rk2, nr rows): partition
+// bounds, table offsets, clearing and the build, run after both partition passes
+// and right before the probe. (Run beside or before S's partition pass, the build
+// was slower: the streaming partition pass evicts the tables being filled from L2.)
+struct L2Tables {
+  int64_t* roff;
+  int64_t* toff;
+  int32_t* table;
+};
+
+template <typename K>
+gj_status l2_tables_run(const Ctx& ctx, Scratch& scr, const K* rk2, int64_t nr, L2Tables* t) {
+  constexpr int kW = L2Slot<K>::kWords;  // int32 words per entry
+  t->roff = scr.get_as<int64_t>(kL2Parts + 1);
+  t->toff = scr.get_as<int64_t>(kL2Parts + 1);
+  t->table = scr.get_as<int32_t>(((size_t)4 * nr + 2 * kL2Parts) * kW);  // sizes < 4 rows + 2 each
+  int* bcounter = scr.get_as<int>(1);
+  if (scr.failed()) return GJ_ERR_OOM;
+  gj_status st;
+  cudaStream_t s = ctx.stream;
+  if ((st = cuda_check(cudaMemsetAsync(bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
+  if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk2, nr, 0, kL2Bits, kHashed, t->roff)) !=
+      GJ_OK)
+    return st;
+  {
+    LaunchScope ls(ctx, KK_PART_BOUNDS);
+    l2_table_offsets_kernel<<<1, kL2Parts, 0, s>>>(t->roff, t->toff);
+  }
+  LaunchScope ls(ctx, KK_NPHJ_BUILD);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((4 * nr + 1023) / 1024, (int64_t)ctx.num_sms * 8));
+  l2_table_clear_kernel<<<blocks, 256, 0, s>>>(t->table, t->toff, kW);
+  // blocks take build chunks in order: the tables being filled are those of a few
+  // neighbouring partitions
+  const int bblocks =
+      (int)std::max<int64_t>(1, std::min<int64_t>((nr + kL2BuildChunk - 1) / kL2BuildChunk, (int64_t)ctx.num_sms * 8));
+  l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk2, nr, t->toff, t->table, bcounter, ctx.d_status);
+  return cuda_check(cudaGetLastError());
+}
+
 template <typename K>
 gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int variant, int bits, int bpp, bool l2,
                      gj_table* T, int64_t cap, int64_t* d_count) {
@@ -1483,6 +1545,7 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
 
   // ---- partitioned hash joins
   const bool gftr = variant == GJ_JOIN_PHJ_TR;
+  L2Tables l2t{};
   const K* rk = (const K*)R->key;
   const K* sk = (const K*)S->key;
   if (bits > 0) {
@@ -1529,6 +1592,7 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, sk, sk2, sc, ns, 0, bits, kHashed,
                                   bpp)) != GJ_OK)
       return st;
+    if (l2 && (st = l2_tables_run<K>(ctx, scr, rk2, nr, &l2t)) != GJ_OK) return st;
     rk = rk2;
     sk = sk2;
     if (gftr) {
@@ -1548,10 +1612,13 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
     for (int c = 0; c < R->ncols; ++c) io.rsrc[c] = R->cols[c];
     for (int c = 0; c < S->ncols; ++c) io.ssrc[c] = S->cols[c];
   }
-  int64_t* roff = scr.get_as<int64_t>(((size_t)1 << bits) + 1);
-  if (scr.failed()) return GJ_ERR_OOM;
-  if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, nr, 0, bits, kHashed, roff)) != GJ_OK)
-    return st;
+  int64_t* roff = l2t.roff;
+  if (!l2) {
+    roff = scr.get_as<int64_t>(((size_t)1 << bits) + 1);
+    if (scr.failed()) return GJ_ERR_OOM;
+    if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, nr, 0, bits, kHashed, roff)) != GJ_OK)
+      return st;
+  }
   // probe keys arrive by bulk copy when S' keys are 16-byte aligned
   io.stage_bulk = (reinterpret_cast<uintptr_t>(sk) & 15) == 0 ? 1 : 0;
   io.narrow4 = io.nr_cols >= 1 && io.nr_cols <= 4 && io.ns_cols >= 1 && io.ns_cols <= 4;
@@ -1564,28 +1631,9 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if ((st = cuda_check(cudaMemsetAsync(ustat, 0, sizeof(uint64_t) * nunits, s))) != GJ_OK) return st;
   if ((st = cuda_check(cudaMemsetAsync(ucounter, 0, sizeof(int), s))) != GJ_OK) return st;
   if (l2) {
-    // one table per L2-sized build partition, then the probe units
-    int64_t* toff = scr.get_as<int64_t>(kL2Parts + 1);
-    constexpr int kW = L2Slot<K>::kWords;  // int32 words per entry
-    int32_t* table = scr.get_as<int32_t>(((size_t)4 * nr + 2 * kL2Parts) * kW);  // sizes < 4 rows + 2 each
-    int* bcounter = scr.get_as<int>(1);
-    if (scr.failed()) return GJ_ERR_OOM;
-    if ((st = cuda_check(cudaMemsetAsync(bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
-    {
-      LaunchScope ls(ctx, KK_PART_BOUNDS);
-      l2_table_offsets_kernel<<<1, kL2Parts, 0, s>>>(roff, toff);
-    }
-    {
-      LaunchScope ls(ctx, KK_NPHJ_BUILD);
-      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((4 * nr + 1023) / 1024, (int64_t)ctx.num_sms * 8));
-      l2_table_clear_kernel<<<blocks, 256, 0, s>>>(table, toff, kW);
-      const int bblocks =
-          (int)std::max<int64_t>(1, std::min<int64_t>((nr + kL2BuildChunk - 1) / kL2BuildChunk, (int64_t)ctx.num_sms * 8));
-      l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk, nr, toff, table, bcounter, ctx.d_status);
-    }
     LaunchScope ls(ctx, KK_PHJ_PROBE);
-    phj_l2_probe_kernel<K><<<(unsigned)nunits, kThreads, 0, s>>>(rk, toff, table, sk, ns, io, ustat, ucounter, nunits,
-                                                                  ctx.d_status);
+    phj_l2_probe_kernel<K><<<(unsigned)nunits, kThreads, 0, s>>>(rk, l2t.toff, l2t.table, sk, ns, io, ustat, ucounter,
+                                                                  nunits, ctx.d_status);
     return cuda_check(cudaGetLastError());
   }
   const size_t dyn = phj_unit_smem_bytes<K>();
@@ -1792,7 +1840,8 @@ int heuristic_join_variant(const gj_table* R, const gj_options* opt) {
 int resolve_join_variant(const gj_table* R, const gj_table* S, int nagg, const gj_options* opt, bool fused) {
   int variant = opt->join_variant;
   if (variant == GJ_JOIN_AUTO && opt->selector == GJ_SELECT_MLP) variant = mlp_choose(R, S, nagg, opt, true, fused);
-  if (variant == GJ_JOIN_AUTO) variant = heuristic_join_variant(R, opt);
+  if (variant == GJ_JOIN_AUTO)
+    variant = opt->selector == GJ_SELECT_HEURISTIC ? heuristic_join_variant(R, opt) : cost_join_variant(R, S, opt, fused);
   return variant;
 }
 

@@ -45,6 +45,15 @@ class Options(ctypes.Structure):
                 ("groups_hint", ctypes.c_int64)]
 
 
+SELECT = {"heuristic": 0, "mlp": 1, "cost": 2}
+
+
+class CostParams(ctypes.Structure):
+    _fields_ = [("bg_over_br", ctypes.c_double), ("bg_over_bl2", ctypes.c_double), ("l2_bytes", ctypes.c_double),
+                ("smem_bytes", ctypes.c_double), ("launch_bytes", ctypes.c_double), ("sync_bytes", ctypes.c_double),
+                ("hot_row_bytes", ctypes.c_double), ("num_sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class ColRef(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int32), ("col", ctypes.c_int32), ("modulus", ctypes.c_int64)]
 
@@ -165,7 +174,8 @@ def _load_batch(lib):
     if getattr(lib, "_batch_ready", False):
         return
     P = ctypes.POINTER
-    lib.gj_batch_create.argtypes = [P(Query), ctypes.c_int32, P(BatchConfig), P(ctypes.c_void_p), ctypes.c_void_p]
+    lib.gj_batch_create.argtypes = [P(Query), ctypes.c_int32, P(BatchConfig), P(Options), P(ctypes.c_void_p),
+                                    ctypes.c_void_p]
     lib.gj_batch_create.restype = ctypes.c_int32
     lib.gj_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.gj_batch_launch.restype = ctypes.c_int32
@@ -173,6 +183,8 @@ def _load_batch(lib):
     lib.gj_batch_get_config.restype = ctypes.c_int32
     lib.gj_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.gj_batch_destroy.restype = ctypes.c_int32
+    lib.gj_batch_get_variants.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.gj_batch_get_variants.restype = ctypes.c_int32
     lib._batch_ready = True
 
 
@@ -180,9 +192,13 @@ class BatchPlan:
     """Many join -> group-by queries run as one persistent launch (gj_batch_*).
 
     Each query is (rkey, rcols, skey, scols, group_key, aggs, agg_cols) with the
-    conventions of join_groupby; outputs are allocated here and kept alive."""
+    conventions of join_groupby; outputs are allocated here and kept alive. Each
+    query's join variant is `variant`, or with "auto" the choice of `selector`
+    (None: the library default) under the given hints; queries that do not run
+    the non-partitioned join in the persistent kernel run one at a time after it."""
 
-    def __init__(self, queries, config=None):
+    def __init__(self, queries, config=None, *, variant: str = "auto", selector=None,
+                 match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, groups_hint: int = 0):
         lib = load()
         _load_batch(lib)
         self._keep = []
@@ -197,7 +213,7 @@ class BatchPlan:
             for j, (a, ref) in enumerate(zip(aggs, agg_cols)):
                 q.ops[j] = AGG[a] if isinstance(a, str) else int(a)
                 q.agg_cols[j] = ColRef(*[int(x) for x in ref])
-            cap = max(1, 2 * int(gk[2]) - 1)
+            cap = max(1, 2 * int(gk[2]) - 1) if int(gk[2]) > 0 else max(1, skey.numel())
             okeys = torch.empty(cap, dtype=torch.int64, device=rkey.device)
             oaggs = [torch.empty(cap, dtype=torch.int64, device=rkey.device) for _ in aggs]
             ng = torch.zeros(1, dtype=torch.int64, device=rkey.device)
@@ -209,14 +225,23 @@ class BatchPlan:
             self.outputs.append((okeys, oaggs, ng))
             self._keep.append((rkey, rcols, skey, scols))
         cfg = BatchConfig(*(config or (0, 0, 0, 0)))
+        o = options(join=variant, sync=False, selector=selector, match_ratio_hint=match_ratio_hint,
+                    zipf_hint=zipf_hint, groups_hint=groups_hint)
         plan = ctypes.c_void_p()
-        _raise(lib.gj_batch_create(arr, len(queries), ctypes.byref(cfg), ctypes.byref(plan), _stream()),
-               "gj_batch_create")
+        _raise(lib.gj_batch_create(arr, len(queries), ctypes.byref(cfg), ctypes.byref(o), ctypes.byref(plan),
+                                   _stream()), "gj_batch_create")
         self._plan = plan
         self._lib = lib
+        self._nq = len(queries)
 
     def launch(self):
         _raise(self._lib.gj_batch_launch(self._plan, _stream()), "gj_batch_launch")
+
+    def variants(self):
+        """The gj_join_variant each query runs."""
+        v = (ctypes.c_int32 * max(1, self._nq))()
+        _raise(self._lib.gj_batch_get_variants(self._plan, ctypes.cast(v, ctypes.c_void_p)), "gj_batch_get_variants")
+        return [int(v[i]) for i in range(self._nq)]
 
     def config(self):
         c = BatchConfig()
@@ -261,8 +286,13 @@ def _load_mlp(lib):
     lib.gj_query_features.argtypes = [P(Table), P(Table), i32, P(Options), p]
     lib.gj_heuristic_choose.argtypes = [P(Table), P(Table), i32, P(Options), P(i32), P(i32)]
     lib.gj_auto_variants.argtypes = [P(Table), P(Table), i32, p, P(Options), i32, P(i32), P(i32)]
+    lib.gj_cost_params_default.argtypes = [P(CostParams)]
+    lib.gj_cost_params_default.restype = None
+    lib.gj_set_cost_params.argtypes = [P(CostParams)]
+    lib.gj_cost_estimate.argtypes = [P(Table), P(Table), i32, p, P(Options), p, p]
     for f in ("gj_mlp_forward", "gj_mlp_loss_grad", "gj_mlp_adam_step", "gj_mlp_sgd_step", "gj_mlp_select",
-              "gj_selector_set", "gj_query_features", "gj_heuristic_choose", "gj_auto_variants"):
+              "gj_selector_set", "gj_query_features", "gj_heuristic_choose", "gj_auto_variants",
+              "gj_set_cost_params", "gj_cost_estimate"):
         getattr(lib, f).restype = i32
     lib._mlp_ready = True
 
@@ -368,21 +398,73 @@ def heuristic_choose(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups
     return jv.value, gv.value
 
 
-def auto_variants(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups, *, selector: int = 0,
-                  fused: bool = False, join: str = "auto", groupby: str = "auto"):
+def _ops_array(ops):
+    if ops is None:
+        return None, None
+    arr = (ctypes.c_int32 * len(ops))(*[AGG[a] if isinstance(a, str) else int(a) for a in ops])
+    return arr, ctypes.cast(arr, ctypes.c_void_p)
+
+
+def auto_variants(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups, *, selector=None,
+                  fused: bool = False, join: str = "auto", groupby: str = "auto", ops=None):
     """(join variant, group-by variant) that AUTO requests run (gj_auto_variants):
     the join of gj_join (fused = False) or gj_join_groupby (fused = True), the
-    group-by of gj_groupby over the S-shaped input; host only."""
+    group-by of gj_groupby over the S-shaped input with aggregates `ops` (names
+    or codes; None: SUMs); host only."""
     lib = load()
     _load_mlp(lib)
     R = _shape_table(nr, key_bytes, ncols_r)
     S = _shape_table(ns, key_bytes, ncols_s)
     o = options(join=join, groupby=groupby, zipf_hint=zipf, match_ratio_hint=mr, groups_hint=int(groups),
                 selector=selector)
+    keep, optr = _ops_array(ops)
     jv, gv = ctypes.c_int32(), ctypes.c_int32()
-    _raise(lib.gj_auto_variants(ctypes.byref(R), ctypes.byref(S), nagg, None, ctypes.byref(o), 1 if fused else 0,
+    _raise(lib.gj_auto_variants(ctypes.byref(R), ctypes.byref(S), nagg, optr, ctypes.byref(o), 1 if fused else 0,
                                 ctypes.byref(jv), ctypes.byref(gv)), "gj_auto_variants")
     return jv.value, gv.value
+
+
+def cost_params_default() -> dict:
+    """The GB300 defaults of the cost model (gj_cost_params_default)."""
+    lib = load()
+    _load_mlp(lib)
+    p = CostParams()
+    lib.gj_cost_params_default(ctypes.byref(p))
+    return {f: getattr(p, f) for f, _ in CostParams._fields_ if f != "reserved"}
+
+
+def set_cost_params(params=None):
+    """Install cost-model parameters (a dict of gj_cost_params fields; missing ones
+    keep their defaults), or with None restore the defaults."""
+    lib = load()
+    _load_mlp(lib)
+    if params is None:
+        _raise(lib.gj_set_cost_params(None), "gj_set_cost_params")
+        return
+    p = CostParams()
+    lib.gj_cost_params_default(ctypes.byref(p))
+    for k, v in params.items():
+        setattr(p, k, v)
+    _raise(lib.gj_set_cost_params(ctypes.byref(p)), "gj_set_cost_params")
+
+
+def cost_estimate(nr, ns, key_bytes, ncols_r, ncols_s, nagg, zipf, mr, groups, *, ops=None):
+    """(join costs [PHJ-TR, PHJ-UR, NPHJ, SMJ-TR, SMJ-UR], group-by costs [HGB, SGB,
+    PGB, SGB-UR, PGB-UR, SGB-DE]) in bytes at B_G (gj_cost_estimate); host only.
+    nr = None skips the join."""
+    import numpy as np
+    lib = load()
+    _load_mlp(lib)
+    S = _shape_table(ns, key_bytes, ncols_s)
+    R = _shape_table(nr, key_bytes, ncols_r) if nr is not None else None
+    o = options(zipf_hint=zipf, match_ratio_hint=mr, groups_hint=int(groups))
+    keep, optr = _ops_array(ops)
+    jc = np.zeros(5, dtype=np.float64)
+    gc = np.zeros(6, dtype=np.float64)
+    _raise(lib.gj_cost_estimate(ctypes.byref(R) if R is not None else None, ctypes.byref(S), nagg, optr,
+                                ctypes.byref(o), jc.ctypes.data if R is not None else None, gc.ctypes.data),
+           "gj_cost_estimate")
+    return (jc if R is not None else None), gc
 
 
 def profile_enable(on: bool):
@@ -442,7 +524,7 @@ def make_table(key: torch.Tensor, cols) -> Table:
 
 def options(join: str = "auto", groupby: str = "auto", radix_bits: int = 0, bits_per_pass: int = 0,
             sync: bool = True, zipf_hint: float = -1.0, match_ratio_hint: float = -1.0, groups_hint: int = 0,
-            selector: int = 0) -> Options:
+            selector=None) -> Options:
     o = Options()
     load().gj_options_default(ctypes.byref(o))
     o.join_variant = JOIN[join]
@@ -453,7 +535,8 @@ def options(join: str = "auto", groupby: str = "auto", radix_bits: int = 0, bits
     o.zipf_hint = zipf_hint
     o.match_ratio_hint = match_ratio_hint
     o.groups_hint = groups_hint
-    o.selector = selector
+    if selector is not None:  # else the library's default (the cost model)
+        o.selector = SELECT[selector] if isinstance(selector, str) else selector
     return o
 
 
@@ -513,7 +596,7 @@ def radix_partition_noalloc(key: torch.Tensor, cols, bit_lo: int, bit_hi: int, t
 
 def join(rkey, rcols, skey, scols, *, variant: str = "phj_tr", capacity: int | None = None,
          radix_bits: int = 0, bits_per_pass: int = 0, sync: bool = True, out=None, count=None,
-         match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, selector: int = 0):
+         match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, selector=None):
     """R join S on key (Sec. 2.2). Returns (T.key, [T.cols: R's then S's], device count tensor).
 
     variant: "auto", "phj_tr", "phj_ur", "nphj", "smj_tr", "smj_ur" (R.key unique), or
@@ -555,10 +638,11 @@ def _agg_arrays(aggs, n_out, device, capacity):
 
 
 def groupby(key, vals, aggs, agg_cols, *, variant: str = "hgb", capacity: int | None = None,
-            radix_bits: int = 0, sync: bool = True, groups_hint: int = 0, zipf_hint: float = -1.0):
+            radix_bits: int = 0, sync: bool = True, groups_hint: int = 0, zipf_hint: float = -1.0, selector=None):
     """GROUP BY key (Sec. 2.2, Alg. 1). Returns (keys, [int64 aggregate columns], device group count).
 
-    variant: "auto", "hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"."""
+    variant: "auto", "hgb", "sgb", "pgb", "sgb_ur", "pgb_ur", "sgb_de"; selector: how "auto"
+    chooses ("heuristic", "mlp", "cost" or a gj_selector_mode; None = the library default)."""
     lib = load()
     t = make_table(key, vals)
     if capacity is None:
@@ -567,16 +651,19 @@ def groupby(key, vals, aggs, agg_cols, *, variant: str = "hgb", capacity: int | 
     oc = (ctypes.c_int32 * len(aggs))(*[int(c) for c in agg_cols])
     okeys = torch.empty(capacity, dtype=key.dtype, device=key.device)
     ng = torch.zeros(1, dtype=torch.int64, device=key.device)
-    o = options(groupby=variant, radix_bits=radix_bits, sync=sync, groups_hint=groups_hint, zipf_hint=zipf_hint)
+    o = options(groupby=variant, radix_bits=radix_bits, sync=sync, groups_hint=groups_hint, zipf_hint=zipf_hint,
+                selector=selector)
     _raise(lib.gj_groupby(ctypes.byref(t), len(aggs), ops, oc, ctypes.byref(o), okeys.data_ptr(), ptrs, capacity,
                           ctypes.c_void_p(ng.data_ptr()), _stream()), "gj_groupby")
     return okeys, outs, ng
 
 
 def join_groupby(rkey, rcols, skey, scols, group_key, aggs, agg_cols, *, variant: str = "auto",
-                 capacity: int | None = None, radix_bits: int = 0, sync: bool = True):
+                 capacity: int | None = None, radix_bits: int = 0, sync: bool = True, selector=None,
+                 match_ratio_hint: float = -1.0, zipf_hint: float = -1.0, groups_hint: int = 0):
     """GROUP BY over R join S without materialising it. group_key / agg_cols are
-    (side, col, modulus) triples (side 0 = R, 1 = S; col -1 = join key)."""
+    (side, col, modulus) triples (side 0 = R, 1 = S; col -1 = join key); selector and
+    hints as for join / groupby."""
     lib = load()
     R = make_table(rkey, rcols)
     S = make_table(skey, scols)
@@ -587,7 +674,8 @@ def join_groupby(rkey, rcols, skey, scols, group_key, aggs, agg_cols, *, variant
     gk = ColRef(*[int(x) for x in group_key])
     okeys = torch.empty(capacity, dtype=torch.int64, device=rkey.device)
     ng = torch.zeros(1, dtype=torch.int64, device=rkey.device)
-    o = options(join=variant, radix_bits=radix_bits, sync=sync)
+    o = options(join=variant, radix_bits=radix_bits, sync=sync, selector=selector, match_ratio_hint=match_ratio_hint,
+                zipf_hint=zipf_hint, groups_hint=groups_hint)
     _raise(lib.gj_join_groupby(ctypes.byref(R), ctypes.byref(S), gk, len(aggs), ops, refs, ctypes.byref(o),
                                okeys.data_ptr(), ptrs, capacity, ctypes.c_void_p(ng.data_ptr()), _stream()),
            "gj_join_groupby")

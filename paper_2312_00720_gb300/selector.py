@@ -205,25 +205,29 @@ def train(records, steps: int = 3000, lr: float = 3e-3, seed: int = 0):
 
 
 def evaluate(records, theta, mean, std) -> dict:
-    """Regret of the network and of the paper's rules on `records`: per query,
-    (t_selected - t_best) / t_best on the combined join + group-by time, t_best
-    over all 5 x 6 variant pairs."""
+    """Regret of the network, of the paper's rules and of the GB300 cost model on
+    `records`: per query, (t_selected - t_best) / t_best on the combined join +
+    group-by time, t_best over all 5 x 6 variant pairs."""
     x, _ = _arrays(records)
     xd = torch.from_numpy(((x - mean) / std).astype(np.float32)).cuda()
     jv, gv = gj.mlp_select(torch.from_numpy(np.asarray(theta, np.float32)).cuda(), xd)
     jv, gv = jv.cpu().numpy(), gv.cpu().numpy()
     jname = {gj.JOIN[v]: v for v in JOIN_VARIANTS}
     gname = {gj.GROUPBY[v]: v for v in GB_VARIANTS}
-    reg_m, reg_h = [], []
+    reg_m, reg_h, reg_c = [], [], []
     for r, a, b in zip(records, jv, gv):
         best = min(r["ms"][v] for v in JOIN_VARIANTS) + min(r["ms"][v] for v in GB_VARIANTS)
         reg_m.append((r["ms"][jname[int(a)]] + r["ms"][gname[int(b)]]) / best - 1.0)
         hj, hg = gj.heuristic_choose(*_shape(r["point"]))
         reg_h.append((r["ms"][jname[hj]] + r["ms"][gname[hg]]) / best - 1.0)
-    reg_m, reg_h = np.array(reg_m), np.array(reg_h)
+        cj, cg = gj.auto_variants(*_shape(r["point"]), selector="cost", ops=GB_AGGS)
+        reg_c.append((r["ms"][jname[cj]] + r["ms"][gname[cg]]) / best - 1.0)
+    reg_m, reg_h, reg_c = np.array(reg_m), np.array(reg_h), np.array(reg_c)
     return {"n": len(records), "mlp_mean_regret": float(reg_m.mean()), "mlp_p90_regret": float(np.quantile(reg_m, 0.9)),
             "heuristic_mean_regret": float(reg_h.mean()),
-            "heuristic_p90_regret": float(np.quantile(reg_h, 0.9))}
+            "heuristic_p90_regret": float(np.quantile(reg_h, 0.9)),
+            "cost_model_mean_regret": float(reg_c.mean()),
+            "cost_model_p90_regret": float(np.quantile(reg_c, 0.9))}
 
 
 def summarize(records) -> dict:
@@ -250,6 +254,7 @@ def main(argv=None):
     ap.add_argument("--points", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=2025)
     ap.add_argument("--budget-s", type=float, default=0.0, help="stop sweeping after this many seconds (0 = none)")
+    ap.add_argument("--save", metavar="NPZ", help="with --evaluate: write the trained network (theta, mean, std)")
     args = ap.parse_args(argv)
     gj.load()
     if args.sweep:
@@ -279,8 +284,25 @@ def main(argv=None):
         train_r, held = split(recs, 0.8, seed=1)
         theta, mean, std, losses = train(train_r, steps=6000)
         ev = evaluate(held, theta, mean, std)
+        if args.save:
+            np.savez(args.save, theta=np.asarray(theta, np.float32), mean=np.asarray(mean, np.float64),
+                     std=np.asarray(std, np.float64))
         print(json.dumps({"evaluation": ev, "train_points": len(train_r), "loss_first_last": [losses[0], losses[-1]],
                           "summary": summarize(recs)}))
+
+
+# The network trained on 80 % of the 4096-point GB300 sweep (grid(4096, seed=2025)),
+# shipped with the package: install_trained() makes it the GJ_SELECT_MLP selector.
+TRAINED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_gb300.npz")
+
+
+def install_trained(path: str = TRAINED) -> bool:
+    """Install the shipped network (gj_selector_set); False if the file is absent."""
+    if not os.path.exists(path):
+        return False
+    z = np.load(path)
+    gj.selector_set(z["theta"], z["mean"], z["std"])
+    return True
 
 
 if __name__ == "__main__":

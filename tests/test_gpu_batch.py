@@ -92,3 +92,61 @@ def test_batch_512_full_config(gj):
         assert aggs[0].sum() == len(w["skey"])            # every S row matches once
         assert aggs[1].sum() == w["scols"][0].astype(np.int64).sum()
     plan.close()
+
+
+def test_batch_runs_each_query_with_its_chosen_variant(gj):
+    """Queries outside the persistent kernel's limits (int64 keys, a modulus above
+    2^20) and queries whose chosen variant is partitioned run one at a time after
+    it; every query still equals the oracle, on two launches."""
+    ws = [wl.join_workload(3000, 12000, 2, 2, seed=11),
+          wl.join_workload(3000, 12000, 2, 2, key_dtype=np.int64, seed=12),
+          wl.join_workload(200_000, 800_000, 2, 2, seed=13),
+          wl.join_workload(5000, 20000, 2, 2, mr=0.5, seed=14)]
+    for w, m in zip(ws, [64, 1000, 1 << 21, 7]):
+        w["modulus"] = m
+    plan = gj.BatchPlan(make_queries(ws), selector="cost")
+    v = plan.variants()
+    assert v[0] == v[3] == 3 and v[1] in (1, 2, 3) and v[2] in (1, 2, 3)
+    for _ in range(2):
+        plan.launch()
+    got = plan.results()
+    assert gj.device_status() == 0
+    for w, (keys, aggs, g) in zip(ws, got):
+        assert np.array_equal(as_rows(keys, aggs), expected(w))
+    plan.close()
+
+
+@pytest.mark.parametrize("variant", ["phj_tr", "phj_ur"])
+def test_batch_with_an_explicit_partitioned_variant_runs_every_query_alone(gj, small_batch, variant):
+    qs = small_batch[:12]
+    plan = gj.BatchPlan(make_queries(qs), variant=variant)
+    assert plan.variants() == [gj.JOIN[variant]] * len(qs)
+    plan.launch()
+    got = plan.results()
+    assert gj.device_status() == 0
+    for w, (keys, aggs, g) in zip(qs, got):
+        assert np.array_equal(as_rows(keys, aggs), expected(w))
+    plan.close()
+
+
+def test_batch_follows_an_installed_network(gj, small_batch):
+    """A network preferring PHJ-UR for every query sends every query through the
+    one-query path; removed again, the default choice is the persistent kernel's
+    non-partitioned join for these small instances."""
+    from oracle import mlp
+    p = mlp.unpack(np.zeros(gj.MLP_PARAMS))
+    b3 = np.ones(mlp.D_OUT)
+    b3[1] = -1.0          # y1: PHJ-UR
+    gj.selector_set(mlp.pack({**p, "b3": b3}).astype(np.float32), np.zeros(12), np.ones(12))
+    try:
+        plan = gj.BatchPlan(make_queries(small_batch[:6]), selector="mlp")
+        assert plan.variants() == [2] * 6
+        plan.launch()
+        for w, (keys, aggs, g) in zip(small_batch[:6], plan.results()):
+            assert np.array_equal(as_rows(keys, aggs), expected(w))
+        plan.close()
+    finally:
+        gj.selector_set(None, None, None)
+    plan = gj.BatchPlan(make_queries(small_batch[:6]), selector="cost")
+    assert plan.variants() == [3] * 6
+    plan.close()
