@@ -348,10 +348,11 @@ __global__ void __launch_bounds__(1024, 1) hgb_aggregate_kernel(const K* __restr
   int ncopy = 1;
   while (use_smem && ncopy < nwarps && 2 * ncopy * copy_bytes <= smem_budget) ncopy *= 2;
   const int warp = threadIdx.x >> 5;
-  // split SUMs (32-bit atomics only) for up to 1024 groups, folded into the result
-  // every epoch: a copy takes at most (nwarps / ncopy) * 32 * kBatch rows per step
+  // split SUMs (32-bit atomics only) whenever the slots are in shared memory,
+  // folded into the result every epoch: a copy takes at most (nwarps / ncopy) * 32 *
+  // kBatch rows per step
   constexpr int kBatch = 4;  // rows per thread per step: loads and lookups of the batch overlap
-  const bool split = use_smem && g <= 1024;
+  const bool split = use_smem;
   const int epoch_steps = (int)(kSplitRows / ((nwarps / ncopy) * 32 * kBatch));
   if (threadIdx.x == 0) {
     int64_t o = 0;

@@ -676,7 +676,7 @@ struct L2Slot<int64_t> {
 
 // Build: blocks take chunks of R' in order from a counter, so the tables being
 // filled at any time are those of a few neighbouring partitions (in L2).
-constexpr int kL2BuildChunk = 4096;
+constexpr int kL2BuildChunk = 1024;  // rows per build chunk (measured: 0.74 ms at 2^25 rows, 0.94 ms for 4096, 1.05 ms for 256)
 template <typename K>
 __global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rkey, int64_t nr,
                                                        const int64_t* __restrict__ toff, int32_t* __restrict__ table,
