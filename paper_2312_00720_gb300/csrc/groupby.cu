@@ -107,7 +107,14 @@ __device__ __forceinline__ int32_t hgb_find(const HEntry<K>* __restrict__ ht, ui
 // block. 4-byte keys are tagged with bit 32 (empty = 0); 8-byte keys are stored as
 // they are (empty = INT64_MIN, a key of that value is simply never cached).
 constexpr int kSeenSlots = 16384;  // 192 KB with the rows: one 1024-thread block per SM
-constexpr int kSeenProbes = 4;
+// Probes of the set per key: when the expected groups fit in half the set, every
+// distinct key of a block must find a slot, or each of its rows goes to the global
+// table (4 probes left a few percent of 4096 keys uncached and made the pass 7x
+// slower); when they do not, the set caches only some keys and a key absent from
+// it is looked for briefly (long probe runs of one lane stall its whole warp:
+// 32 probes made the 2^20-group pass 1.8x slower).
+constexpr int kSeenProbesFit = 32;
+constexpr int kSeenProbesSome = 4;
 template <typename K>
 __device__ __forceinline__ unsigned long long seen_tag(K k) {
   return sizeof(K) == 4 ? ((1ull << 32) | (uint64_t)(uint32_t)k) : (unsigned long long)(int64_t)k;
@@ -123,7 +130,7 @@ __device__ __forceinline__ unsigned long long seen_empty() {
 // table at once. At the end all threads of the block insert the collected keys
 // together, so the global round trips run in full warps rather than one diverged
 // lane at a time.
-template <typename K>
+template <typename K, int kProbes>
 __global__ void __launch_bounds__(1024, 1) hgb_dict_kernel(const K* __restrict__ key, int64_t n, HEntry<K>* ht,
                                                        uint64_t mask, unsigned long long* ngroups,
                                                        K* __restrict__ out_keys, int64_t cap, const int* gate,
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(1024, 1) hgb_dict_kernel(const K* __restrict__
       bool handled = false;
       if (tag != empty) {
         uint32_t sl = (uint32_t)KeyTraits<K>::hash64(kk[u]) & (kSeenSlots - 1);
-        for (int p = 0; p < kSeenProbes; ++p) {
+        for (int p = 0; p < kProbes; ++p) {
           unsigned long long v = s_seen[sl];
           if (v == empty) {
             if (*(volatile int*)&s_fill >= kSeenSlots / 2) break;  // full enough: look up only
@@ -519,75 +526,92 @@ __global__ void __launch_bounds__(1024, 1) hgb_tiny_kernel(const K* __restrict__
       mx[h][c] = INT32_MIN;
     }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  bool bail = false;
-  // the loop bound is the block's first row: every thread runs the same steps
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i - tid < n; i += stride) {
-    const bool valid = i < n;
-    const K k = valid ? __ldcs(key + i) : K(0);
-    int32_t v[kColCache];
+  bool bail = false, stop = false;
+  // kTB rows per thread per step, their loads in flight together; the loop bound is
+  // the warp's first row, so the lanes of a warp run the same steps (no block
+  // barrier inside the loop: a warp that meets too many keys stops on its own)
+  constexpr int kTB = 2;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + tid; i0 - lane < n && !stop; i0 += stride * kTB) {
+    K kk[kTB];
+    int32_t v[kTB][kColCache];
+    bool valid[kTB];
 #pragma unroll
-    for (int c = 0; c < kColCache; ++c) v[c] = (valid && c < cc.n) ? __ldcs(cc.src[c] + i) : 0;
-    int slot = -1;
-    if (valid) {
-      const unsigned long long tag = seen_tag<K>(k);
-      if (tag != empty) {
-        uint32_t sl = (uint32_t)KeyTraits<K>::hash64(k) & (kTinySlots - 1);
-        for (int p = 0; p < kTinySlots; ++p) {
-          unsigned long long w = ((volatile unsigned long long*)s_tab)[sl];
-          if (w == empty) {
-            w = atomicCAS(&s_tab[sl], empty, tag);
+    for (int u = 0; u < kTB; ++u) {
+      const int64_t i = i0 + u * stride;
+      valid[u] = i < n;
+      kk[u] = valid[u] ? __ldcs(key + i) : K(0);
+#pragma unroll
+      for (int c = 0; c < kColCache; ++c) v[u][c] = (valid[u] && c < cc.n) ? __ldcs(cc.src[c] + i) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kTB; ++u) {
+      int slot = -1;
+      if (valid[u]) {
+        const unsigned long long tag = seen_tag<K>(kk[u]);
+        if (tag != empty) {
+          uint32_t sl = (uint32_t)KeyTraits<K>::hash64(kk[u]) & (kTinySlots - 1);
+          for (int p = 0; p < kTinySlots; ++p) {
+            unsigned long long w = ((volatile unsigned long long*)s_tab)[sl];
             if (w == empty) {
-              if (atomicAdd(&s_nkeys, 1) >= kTinyKeys) bail = true;
+              w = atomicCAS(&s_tab[sl], empty, tag);
+              if (w == empty) {
+                if (atomicAdd(&s_nkeys, 1) >= kTinyKeys) bail = true;
+                slot = (int)sl;
+                break;
+              }
+            }
+            if (w == tag) {
               slot = (int)sl;
               break;
             }
+            sl = (sl + 1) & (kTinySlots - 1);
           }
-          if (w == tag) {
-            slot = (int)sl;
-            break;
+        }
+        if (slot < 0) bail = true;  // INT64_MIN as an 8-byte key, or a full table
+      }
+      if (__any_sync(0xffffffffu, bail)) {  // too many keys for this path
+        stop = true;
+        break;
+      }
+      // the lanes whose row is in slot lane (h = 0) and slot lane + 32 (h = 1)
+      unsigned m0 = __ballot_sync(0xffffffffu, slot >= 0), m1 = m0;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        const unsigned bb = __ballot_sync(0xffffffffu, (slot >> b) & 1);
+        const unsigned sel = ((lane >> b) & 1) ? bb : ~bb;
+        m0 &= sel;
+        m1 &= sel;
+      }
+      const unsigned b5 = __ballot_sync(0xffffffffu, (slot >> 5) & 1);
+      m0 &= ~b5;
+      m1 &= b5;
+      cnt[0] += __popc(m0);
+      cnt[1] += __popc(m1);
+      const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)max(__popc(m0), __popc(m1)));
+      for (int r = 0; r < rounds; ++r) {
+        const int s0 = m0 ? __ffs(m0) - 1 : lane, s1 = m1 ? __ffs(m1) - 1 : lane;
+#pragma unroll
+        for (int c = 0; c < kColCache; ++c) {
+          const int32_t x0 = __shfl_sync(0xffffffffu, v[u][c], s0), x1 = __shfl_sync(0xffffffffu, v[u][c], s1);
+          if (m0) {
+            sum[0][c] += x0;
+            mn[0][c] = min(mn[0][c], x0);
+            mx[0][c] = max(mx[0][c], x0);
           }
-          sl = (sl + 1) & (kTinySlots - 1);
+          if (m1) {
+            sum[1][c] += x1;
+            mn[1][c] = min(mn[1][c], x1);
+            mx[1][c] = max(mx[1][c], x1);
+          }
         }
+        m0 &= m0 - 1;
+        m1 &= m1 - 1;
       }
-      if (slot < 0) bail = true;  // INT64_MIN as an 8-byte key, or a full table
-    }
-    if (__syncthreads_or(bail)) break;  // too many keys for this path
-    // the lanes whose row is in slot lane (h = 0) and slot lane + 32 (h = 1)
-    unsigned m0 = __ballot_sync(0xffffffffu, slot >= 0), m1 = m0;
-#pragma unroll
-    for (int b = 0; b < 5; ++b) {
-      const unsigned bb = __ballot_sync(0xffffffffu, (slot >> b) & 1);
-      const unsigned sel = ((lane >> b) & 1) ? bb : ~bb;
-      m0 &= sel;
-      m1 &= sel;
-    }
-    const unsigned b5 = __ballot_sync(0xffffffffu, (slot >> 5) & 1);
-    m0 &= ~b5;
-    m1 &= b5;
-    cnt[0] += __popc(m0);
-    cnt[1] += __popc(m1);
-    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)max(__popc(m0), __popc(m1)));
-    for (int r = 0; r < rounds; ++r) {
-      const int s0 = m0 ? __ffs(m0) - 1 : lane, s1 = m1 ? __ffs(m1) - 1 : lane;
-#pragma unroll
-      for (int c = 0; c < kColCache; ++c) {
-        const int32_t x0 = __shfl_sync(0xffffffffu, v[c], s0), x1 = __shfl_sync(0xffffffffu, v[c], s1);
-        if (m0) {
-          sum[0][c] += x0;
-          mn[0][c] = min(mn[0][c], x0);
-          mx[0][c] = max(mx[0][c], x0);
-        }
-        if (m1) {
-          sum[1][c] += x1;
-          mn[1][c] = min(mn[1][c], x1);
-          mx[1][c] = max(mx[1][c], x1);
-        }
-      }
-      m0 &= m0 - 1;
-      m1 &= m1 - 1;
     }
   }
-  if (s_nkeys > kTinyKeys || __syncthreads_or(bail)) {
+  // every warp has left the loop before the key count is read
+  const bool any_bail = __syncthreads_or(bail);
+  if (any_bail || s_nkeys > kTinyKeys) {
     if (tid == 0) atomicExch(overflow, 1);
     return;
   }
@@ -1547,10 +1571,11 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     // one block per SM with its key cache
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms));
     const int cache_bytes = kSeenSlots * (int)(sizeof(unsigned long long) + sizeof(int32_t));
-    if ((st = ensure_smem_attr(ctx, (const void*)hgb_dict_kernel<K>, cache_bytes)) != GJ_OK) return st;
-    hgb_dict_kernel<K><<<blocks, 1024, cache_bytes, s>>>((const K*)in->key, n, ht, slots - 1,
-                                                         (unsigned long long*)d_ngroups, (K*)out_keys, cap, gate,
-                                                         ctx.d_status);
+    const bool fit = opt->groups_hint > 0 && opt->groups_hint <= kSeenSlots / 2;
+    auto kern = fit ? hgb_dict_kernel<K, kSeenProbesFit> : hgb_dict_kernel<K, kSeenProbesSome>;
+    if ((st = ensure_smem_attr(ctx, (const void*)kern, cache_bytes)) != GJ_OK) return st;
+    kern<<<blocks, 1024, cache_bytes, s>>>((const K*)in->key, n, ht, slots - 1, (unsigned long long*)d_ngroups,
+                                           (K*)out_keys, cap, gate, ctx.d_status);
   }
 
   if (variant == GJ_GB_HGB) {

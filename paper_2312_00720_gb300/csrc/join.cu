@@ -322,40 +322,14 @@ __device__ __forceinline__ void emit_cols(const JoinIO& io, int c, int g, bool r
   }
 }
 
-// Output offset of a probe unit (decoupled look-back over units) and the
-// materialisation of its matches: s_midx[r] is the build row of unit row r (or
-// -1). Every warp owns a contiguous range of the unit and writes it without
-// block barriers, all loads of a group of columns in flight before its stores.
-// Called by all threads of the block after s_midx is complete.
+// One warp materialises unit rows [w0, wend) (s_midx[r]: the build row of unit
+// row r, or -1) at output positions from `pos` on, in row order; all loads of a
+// group of columns are in flight before its stores. Returns true when a match fell
+// beyond the output capacity (its row is dropped).
 template <typename K>
-__device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_t u0, int un, int64_t unit,
-                                              int64_t nunits, const int32_t* s_midx, const JoinIO& io,
-                                              uint64_t* unit_status, int* err, uint32_t* s_wcnt, uint64_t* s_base_p) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint64_t& s_base = *s_base_p;
-  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
-  const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
-  uint32_t cnt = 0;
-  for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane == 0) s_wcnt[warp] = cnt;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
-    if (lane == 0) {
-      s_base = excl;
-      if (unit == nunits - 1 && io.d_count) *io.d_count = (int64_t)(excl + tot);
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 2: each warp materialises its range, no block barriers
-  int64_t pos = (int64_t)s_base;
-  for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+__device__ __forceinline__ bool emit_range(const K* __restrict__ skey, int64_t u0, int w0, int wend, int64_t pos,
+                                           const int32_t* s_midx, const JoinIO& io) {
+  const int lane = threadIdx.x & 31;
   const int64_t cap = io.cap;
   const unsigned lt = (1u << lane) - 1;
   const int ncols = io.nr_cols + io.ns_cols;
@@ -454,7 +428,44 @@ __device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_
       c += g;
     }
   }
-  if (overflow) set_status(err, GJ_ERR_CAPACITY);
+  return overflow;
+}
+
+// Output offset of a probe unit (decoupled look-back over units) and the
+// materialisation of its matches: s_midx[r] is the build row of unit row r (or
+// -1). Every warp owns a contiguous range of the unit and writes it without
+// block barriers, all loads of a group of columns in flight before its stores.
+// Called by all threads of the block after s_midx is complete.
+template <typename K>
+__device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_t u0, int un, int64_t unit,
+                                              int64_t nunits, const int32_t* s_midx, const JoinIO& io,
+                                              uint64_t* unit_status, int* err, uint32_t* s_wcnt, uint64_t* s_base_p) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint64_t& s_base = *s_base_p;
+  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
+  const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
+  uint32_t cnt = 0;
+  for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) s_wcnt[warp] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
+    if (lane == 0) {
+      s_base = excl;
+      if (unit == nunits - 1 && io.d_count) *io.d_count = (int64_t)(excl + tot);
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: each warp materialises its range, no block barriers
+  int64_t pos = (int64_t)s_base;
+  for (int w = 0; w < warp; ++w) pos += s_wcnt[w];
+  if (emit_range<K>(skey, u0, w0, wend, pos, s_midx, io)) set_status(err, GJ_ERR_CAPACITY);
 }
 
 template <typename K>
