@@ -251,6 +251,28 @@ def bench_gather(gj, steps: int = 10):
             "clustered_gb_s": 12 * n / (tc * 1e-3) / 1e9}
 
 
+def bench_selector(gj, n_sample: int = 64):
+    """Variant selection on held-out queries, timed live: the first n_sample of the
+    819 held-out points of the 4096-point grid (grid(4096, seed=2025), the seeded
+    80/20 split the shipped network was trained on), every join and group-by
+    variant timed (median of 3), and the regret of the shipped network, the cost
+    model and the paper's rules against the best of the 5 x 6 pairs."""
+    import numpy as np
+
+    from paper_2312_00720_gb300 import selector as sel
+    pts = sel.grid(4096, seed=2025)
+    _, held = sel.split(pts, 0.8, seed=1)
+    sample = held[:n_sample]
+    t0 = time.perf_counter()
+    recs = [{"point": p, "features": sel.features(p).tolist(), "ms": sel.measure(p, reps=3)} for p in sample]
+    z = np.load(sel.TRAINED)
+    ev = sel.evaluate(recs, z["theta"], z["mean"], z["std"])
+    return {"workload": f"first {len(sample)} of the {len(held)} held-out points of grid(4096, seed=2025), "
+                        "11 variants timed live per point",
+            "n_points": ev["n"], "network": "selector_gb300.npz (trained on the other 3277 points)",
+            **{k: v for k, v in ev.items() if k != "n"}, "seconds": time.perf_counter() - t0}
+
+
 def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 6784.5):
     """One query: |R| = 2^20 ⋈ |S| = 2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay), not materialised."""
     import torch
@@ -723,6 +745,7 @@ def main():
             out["batched"] = bench_batch(gj, wl, cpu=cpu, peak=peak)
             out["many_to_many"] = bench_many_to_many(gj, wl, peak=peak)
             out["gather_calibration"] = bench_gather(gj)
+            out["selector"] = bench_selector(gj)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

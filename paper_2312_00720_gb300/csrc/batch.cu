@@ -43,6 +43,14 @@ constexpr int kSmemAgg = 64 * 1024;
 
 enum TaskKind { TK_ZERO = 0, TK_BUILD = 1, TK_PROBE = 2, TK_EMIT = 3 };
 
+// Shared-memory slots of a probe task. 64-bit shared-memory atomics are
+// compare-and-swap loops that collapse when many lanes hit one slot (a handful
+// of groups), so values that fit 32 bits use 32-bit slots: COUNT, MIN/MAX, and
+// SUM split over two words (the value's low 16 bits unsigned, its high 16 bits
+// signed), exact while a task has at most 65535 rows; merged into the int64
+// results at the end of the task.
+enum SlotKind { SK_COUNT32 = 0, SK_MINMAX32 = 1, SK_SPLIT = 2, SK_64 = 3 };
+
 struct BRef {
   int32_t is_key;
   int32_t side;
@@ -61,8 +69,14 @@ struct BInst {
   unsigned long long* cnt;
   int64_t* agg[kBMaxAggs];
   int64_t nslots, dense_off;
-  int32_t nagg, smem;
+  int32_t nagg, smem;  // smem: the probe aggregates into shared memory (layout below)
   int32_t op[kBMaxAggs];
+  // shared-memory slot form of aggregate j (SlotKind) and its byte offset; the
+  // 32-bit row counts of the slots come first
+  int32_t sform[kBMaxAggs];
+  int32_t soff[kBMaxAggs];
+  int32_t fits32;  // bit j: aggregate j's values fit 32 bits
+  int32_t prows;   // rows per probe task
   BRef gk;
   BRef val[kBMaxAggs];
   int64_t* out_keys;
@@ -138,12 +152,19 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(const BInst* __restric
       block_done(&c[1]);
     } else if (T.kind == TK_PROBE) {
       block_wait(&c[1], (unsigned long long)I.nbuild, err);
-      unsigned long long* s_cnt = (unsigned long long*)s_dyn;
-      int64_t* s_agg = (int64_t*)(s_cnt + I.nslots);
+      uint32_t* s_cnt = (uint32_t*)s_dyn;
       if (I.smem) {
         for (int64_t s = t; s < I.nslots; s += kBThreads) {
-          s_cnt[s] = 0;
-          for (int j = 0; j < I.nagg; ++j) s_agg[j * I.nslots + s] = agg_identity(I.op[j]);
+          s_cnt[s] = 0u;
+          for (int j = 0; j < I.nagg; ++j) {
+            unsigned char* base = s_dyn + I.soff[j];
+            switch (I.sform[j]) {
+              case SK_COUNT32: ((uint32_t*)base)[s] = 0u; break;
+              case SK_MINMAX32: ((int32_t*)base)[s] = I.op[j] == GJ_AGG_MIN ? INT32_MAX : INT32_MIN; break;
+              case SK_SPLIT: ((int64_t*)base)[s] = 0; break;
+              default: ((int64_t*)base)[s] = agg_identity(I.op[j]); break;
+            }
+          }
         }
         __syncthreads();
       }
@@ -164,10 +185,26 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(const BInst* __restric
         if (m < 0) continue;
         const int64_t slot = bref_value(I.gk, m, i, k) + I.dense_off;
         if (I.smem) {
-          atomicAdd(&s_cnt[slot], 1ull);
-          for (int j = 0; j < I.nagg; ++j)
-            agg_atomic(I.op[j], &s_agg[j * I.nslots + slot],
-                       I.op[j] == GJ_AGG_COUNT ? 1 : bref_value(I.val[j], m, i, k));
+          atomicAdd(&s_cnt[slot], 1u);
+          for (int j = 0; j < I.nagg; ++j) {
+            unsigned char* base = s_dyn + I.soff[j];
+            switch (I.sform[j]) {
+              case SK_COUNT32: atomicAdd((uint32_t*)base + slot, 1u); break;
+              case SK_MINMAX32: {
+                const int32_t v = (int32_t)bref_value(I.val[j], m, i, k);
+                if (I.op[j] == GJ_AGG_MIN) atomicMin((int32_t*)base + slot, v); else atomicMax((int32_t*)base + slot, v);
+                break;
+              }
+              case SK_SPLIT: {
+                const int32_t v = (int32_t)bref_value(I.val[j], m, i, k);
+                atomicAdd((uint32_t*)base + 2 * slot, (uint32_t)v & 0xffffu);
+                atomicAdd((int32_t*)base + 2 * slot + 1, v >> 16);
+                break;
+              }
+              default:
+                agg_atomic(I.op[j], (int64_t*)base + slot, I.op[j] == GJ_AGG_COUNT ? 1 : bref_value(I.val[j], m, i, k));
+            }
+          }
         } else {
           atomicAdd(&I.cnt[slot], 1ull);
           for (int j = 0; j < I.nagg; ++j)
@@ -177,9 +214,21 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(const BInst* __restric
       if (I.smem) {
         __syncthreads();
         for (int64_t s = t; s < I.nslots; s += kBThreads) {
-          if (s_cnt[s] == 0) continue;
-          atomicAdd(&I.cnt[s], s_cnt[s]);
-          for (int j = 0; j < I.nagg; ++j) agg_atomic(I.op[j], &I.agg[j][s], s_agg[j * I.nslots + s]);
+          if (s_cnt[s] == 0u) continue;
+          atomicAdd(&I.cnt[s], (unsigned long long)s_cnt[s]);
+          for (int j = 0; j < I.nagg; ++j) {
+            const unsigned char* base = s_dyn + I.soff[j];
+            int64_t v;
+            switch (I.sform[j]) {
+              case SK_COUNT32: v = (int64_t)((const uint32_t*)base)[s]; break;
+              case SK_MINMAX32: v = (int64_t)((const int32_t*)base)[s]; break;
+              case SK_SPLIT:
+                v = (int64_t)((const int32_t*)base)[2 * s + 1] * 65536 + (int64_t)((const uint32_t*)base)[2 * s];
+                break;
+              default: v = ((const int64_t*)base)[s]; break;
+            }
+            agg_atomic(I.op[j], &I.agg[j][s], v);
+          }
         }
       }
       block_done(&c[2]);
@@ -326,9 +375,14 @@ gj_status build_tasks(gj_batch_plan* P, const gj_batch_config& cfg) {
   std::vector<BTask> tasks;
   size_t ctl = 1;  // word 0: queue head
   for (auto& I : P->h_insts) {
+    // rows per probe task (at least four rows per shared-memory slot measured no faster)
+    I.prows = cfg.probe_rows;
+    // a split SUM slot is exact for at most 65535 rows: longer probe tasks take 64-bit SUMs
+    for (int j = 0; j < I.nagg; ++j)
+      if (I.op[j] == GJ_AGG_SUM && ((I.fits32 >> j) & 1)) I.sform[j] = I.prows <= 65535 ? SK_SPLIT : SK_64;
     I.nzero = (int32_t)ceil_div((int64_t)I.ht_slots + I.nslots, kZeroChunk);
     I.nbuild = (int32_t)ceil_div(I.nr, cfg.build_rows);
-    I.nprobe = (int32_t)ceil_div(I.ns, cfg.probe_rows);
+    I.nprobe = (int32_t)ceil_div(I.ns, I.prows);
     I.nemit = (int32_t)ceil_div(I.nslots, kEmitTile);
     I.ctl = (int64_t)ctl;
     ctl += 4 + I.nemit;
@@ -346,8 +400,7 @@ gj_status build_tasks(gj_batch_plan* P, const gj_batch_config& cfg) {
   auto push_p = [&](int q) {
     const BInst& I = P->h_insts[q];
     for (int p = 0; p < I.nprobe; ++p)
-      tasks.push_back({q, TK_PROBE, (int64_t)p * cfg.probe_rows,
-                       std::min<int64_t>(I.ns, (int64_t)(p + 1) * cfg.probe_rows), p, 0});
+      tasks.push_back({q, TK_PROBE, (int64_t)p * I.prows, std::min<int64_t>(I.ns, (int64_t)(p + 1) * I.prows), p, 0});
   };
   auto push_e = [&](int q) {
     const BInst& I = P->h_insts[q];
@@ -483,8 +536,6 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
     I.nslots = 2 * Q.group_key.modulus - 1;
     I.dense_off = Q.group_key.modulus - 1;
     I.nagg = Q.nagg;
-    I.smem = (I.nslots * 8 * (1 + Q.nagg)) <= kSmemAgg;
-    any_smem |= I.smem != 0;
     void* p = nullptr;
     const size_t bytes = sizeof(int32_t) * hs + sizeof(unsigned long long) * I.nslots +
                          sizeof(int64_t) * I.nslots * Q.nagg + 64 * (2 + Q.nagg);
@@ -503,6 +554,27 @@ gj_status gj_batch_create(const gj_query* queries, int32_t nq, const gj_batch_co
       if (Q.ops[j] != GJ_AGG_COUNT) I.val[j] = make_ref(Q, Q.agg_cols[j]);
     }
     I.gk = make_ref(Q, Q.group_key);
+    // shared-memory layout of a probe task: 32-bit row counts, then each aggregate
+    // (32-bit COUNT / MIN / MAX when the values fit 32 bits, else 8 bytes: a split
+    // or 64-bit SUM, 64-bit MIN / MAX)
+    {
+      int64_t off = 4 * I.nslots;
+      for (int j = 0; j < Q.nagg; ++j) {
+        const BRef& v = I.val[j];
+        const bool fits32 = v.is_key || v.size == 4 || (v.mod > 0 && v.mod <= (int64_t(1) << 31));
+        if (fits32) I.fits32 |= 1 << j;
+        int kind = SK_64;
+        if (Q.ops[j] == GJ_AGG_COUNT) kind = SK_COUNT32;
+        else if (fits32) kind = Q.ops[j] == GJ_AGG_SUM ? SK_SPLIT : SK_MINMAX32;
+        const int w = (kind == SK_COUNT32 || kind == SK_MINMAX32) ? 4 : 8;
+        off = (off + w - 1) / w * w;
+        I.sform[j] = kind;
+        I.soff[j] = (int32_t)std::min<int64_t>(off, INT32_MAX);
+        off += (int64_t)w * I.nslots;
+      }
+      I.smem = off <= kSmemAgg;
+      any_smem |= I.smem != 0;
+    }
     I.out_keys = Q.out_keys;
     I.cap = Q.capacity;
     I.d_ngroups = Q.d_ngroups;

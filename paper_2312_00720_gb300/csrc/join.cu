@@ -1369,26 +1369,30 @@ __global__ void __launch_bounds__(kThreads) group_emit_kernel(GroupSink G, int64
 }
 
 // The tables of the L2-sized build partitions of R' (rk2, nr rows): partition
-// bounds, table offsets, clearing and the build, run after both partition passes
-// and right before the probe. (Run beside or before S's partition pass, the build
-// was slower: the streaming partition pass evicts the tables being filled from L2.)
+// bounds, table offsets, clearing and the build (scratch taken up front).
 struct L2Tables {
   int64_t* roff;
   int64_t* toff;
   int32_t* table;
+  int* bcounter;
 };
 
 template <typename K>
-gj_status l2_tables_run(const Ctx& ctx, Scratch& scr, const K* rk2, int64_t nr, L2Tables* t) {
+gj_status l2_tables_alloc(Scratch& scr, int64_t nr, L2Tables* t) {
   constexpr int kW = L2Slot<K>::kWords;  // int32 words per entry
   t->roff = scr.get_as<int64_t>(kL2Parts + 1);
   t->toff = scr.get_as<int64_t>(kL2Parts + 1);
   t->table = scr.get_as<int32_t>(((size_t)4 * nr + 2 * kL2Parts) * kW);  // sizes < 4 rows + 2 each
-  int* bcounter = scr.get_as<int>(1);
-  if (scr.failed()) return GJ_ERR_OOM;
+  t->bcounter = scr.get_as<int>(1);
+  return scr.failed() ? GJ_ERR_OOM : GJ_OK;
+}
+
+template <typename K>
+gj_status l2_tables_run(const Ctx& ctx, const K* rk2, int64_t nr, const L2Tables* t) {
+  constexpr int kW = L2Slot<K>::kWords;
   gj_status st;
   cudaStream_t s = ctx.stream;
-  if ((st = cuda_check(cudaMemsetAsync(bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
+  if ((st = cuda_check(cudaMemsetAsync(t->bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
   if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk2, nr, 0, kL2Bits, kHashed, t->roff)) !=
       GJ_OK)
     return st;
@@ -1403,7 +1407,7 @@ gj_status l2_tables_run(const Ctx& ctx, Scratch& scr, const K* rk2, int64_t nr, 
   // neighbouring partitions
   const int bblocks =
       (int)std::max<int64_t>(1, std::min<int64_t>((nr + kL2BuildChunk - 1) / kL2BuildChunk, (int64_t)ctx.num_sms * 8));
-  l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk2, nr, t->toff, t->table, bcounter, ctx.d_status);
+  l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk2, nr, t->toff, t->table, t->bcounter, ctx.d_status);
   return cuda_check(cudaGetLastError());
 }
 
@@ -1597,13 +1601,16 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
       sc.dst[0] = scr.get((size_t)ns * 4);
     }
     if (scr.failed()) return GJ_ERR_OOM;
+    if (l2 && (st = l2_tables_alloc<K>(scr, nr, &l2t)) != GJ_OK) return st;
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk, rk2, rc, nr, 0, bits, kHashed,
                                   bpp)) != GJ_OK)
       return st;
     if ((st = radix_partition_run(ctx, scr, sizeof(K) == 8 ? GJ_I64 : GJ_I32, sk, sk2, sc, ns, 0, bits, kHashed,
                                   bpp)) != GJ_OK)
       return st;
-    if (l2 && (st = l2_tables_run<K>(ctx, scr, rk2, nr, &l2t)) != GJ_OK) return st;
+    // the build right before the probe: run on a second stream beside S's partition
+    // pass it gained under 1 % (the streaming pass evicts the tables being filled)
+    if (l2 && (st = l2_tables_run<K>(ctx, rk2, nr, &l2t)) != GJ_OK) return st;
     rk = rk2;
     sk = sk2;
     if (gftr) {
