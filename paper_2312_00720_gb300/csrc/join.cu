@@ -655,17 +655,6 @@ __global__ void __launch_bounds__(kL2Parts) l2_table_offsets_kernel(const int64_
   if (p == 0) toff[0] = 0;
 }
 
-__global__ void l2_table_clear_kernel(int32_t* __restrict__ table, const int64_t* __restrict__ toff, int words) {
-  const int64_t total = toff[kL2Parts] * words;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < total; i += stride) {
-    if (i + 4 <= total)
-      *reinterpret_cast<int4*>(table + i) = make_int4(0, 0, 0, 0);  // sizes are powers of two >= 2: 16-byte runs
-    else
-      for (int64_t e = i; e < total; ++e) table[e] = 0;
-  }
-}
-
 // Table entries: for 4-byte keys one 64-bit word, (row + 1) << 32 | key, claimed
 // by a single compare-and-swap, so a probe reads key and row in one access; for
 // 8-byte keys a 32-bit row + 1 with the key compared in R'.
@@ -688,11 +677,54 @@ struct L2Slot<int64_t> {
 // Build: blocks take chunks of R' in order from a counter, so the tables being
 // filled at any time are those of a few neighbouring partitions (in L2).
 constexpr int kL2BuildChunk = 1024;  // rows per build chunk (measured: 0.74 ms at 2^25 rows, 0.94 ms for 4096, 1.05 ms for 256)
+// A partition's table is cleared just before it is filled, by the blocks whose
+// chunks reach it (in segments of kL2ClearWords words taken from a per-partition
+// counter), so its lines are written to L2 and filled there instead of being
+// cleared to DRAM by a separate pass and read back. A chunk covers the partitions
+// of its rows and any empty ones up to the next chunk's first partition; the
+// first and last chunks also cover the partitions before and after all rows.
+constexpr int kL2ClearWords = 8192;  // 32 KB per clearing segment
+
+__device__ __forceinline__ int l2_part_of_hash(uint64_t h) { return (int)(h & (kL2Parts - 1)); }
+
+template <typename K>
+__device__ __forceinline__ void l2_clear_partition(int p, const int64_t* __restrict__ toff, int32_t* table, int kw,
+                                                   int* pseg, int* pdone, int* s_seg, int* err) {
+  const int64_t w0 = toff[p] * kw, w1 = toff[p + 1] * kw;  // even word counts: 8-byte stores
+  const int nseg = (int)((w1 - w0 + kL2ClearWords - 1) / kL2ClearWords);
+  for (;;) {
+    if (threadIdx.x == 0) *s_seg = atomicAdd(&pseg[p], 1);
+    __syncthreads();
+    const int seg = *s_seg;
+    __syncthreads();
+    if (seg >= nseg) break;
+    const int64_t a = w0 + (int64_t)seg * kL2ClearWords, b = min64(w1, a + kL2ClearWords);
+    for (int64_t e = a + 2 * threadIdx.x; e < b; e += 2 * blockDim.x)
+      *reinterpret_cast<uint2*>(table + e) = make_uint2(0u, 0u);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&pdone[p], 1);
+  }
+  // every segment of the partition cleared (by this block or others)
+  if (threadIdx.x == 0) {
+    WaitGuard guard(err);
+    while (*(volatile int*)&pdone[p] < nseg) {
+      if (guard.expired()) {
+        set_status(err, GJ_ERR_TIMEOUT);
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 template <typename K>
 __global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rkey, int64_t nr,
                                                        const int64_t* __restrict__ toff, int32_t* __restrict__ table,
-                                                       int* chunk_counter, int* err) {
+                                                       int* chunk_counter, int* pseg, int* pdone, int* err) {
   __shared__ int64_t s_chunk;
+  __shared__ int s_pa, s_pb, s_seg;
   for (;;) {
     if (threadIdx.x == 0) s_chunk = atomicAdd(chunk_counter, 1);
     __syncthreads();
@@ -700,6 +732,14 @@ __global__ void __launch_bounds__(256) l2_build_kernel(const K* __restrict__ rke
     __syncthreads();
     if (c0 >= nr) return;
     const int64_t c1 = min64(nr, c0 + kL2BuildChunk);
+    if (threadIdx.x == 0) {
+      const int pf = l2_part_of_hash(KeyTraits<K>::hash64(rkey[c0]));
+      const int pl = l2_part_of_hash(KeyTraits<K>::hash64(rkey[c1 - 1]));
+      s_pa = c0 == 0 ? 0 : pf;
+      s_pb = c1 == nr ? kL2Parts - 1 : max(pl, l2_part_of_hash(KeyTraits<K>::hash64(rkey[c1])) - 1);
+    }
+    __syncthreads();
+    for (int p = s_pa; p <= s_pb; ++p) l2_clear_partition<K>(p, toff, table, L2Slot<K>::kWords, pseg, pdone, &s_seg, err);
     if constexpr (sizeof(K) == 4) {
       // one row per thread in flight (batching several rows' compare-and-swaps
       // per thread made the build 1.7x slower)
@@ -1383,16 +1423,16 @@ gj_status l2_tables_alloc(Scratch& scr, int64_t nr, L2Tables* t) {
   t->roff = scr.get_as<int64_t>(kL2Parts + 1);
   t->toff = scr.get_as<int64_t>(kL2Parts + 1);
   t->table = scr.get_as<int32_t>(((size_t)4 * nr + 2 * kL2Parts) * kW);  // sizes < 4 rows + 2 each
-  t->bcounter = scr.get_as<int>(1);
+  t->bcounter = scr.get_as<int>(1 + 2 * kL2Parts);
   return scr.failed() ? GJ_ERR_OOM : GJ_OK;
 }
 
 template <typename K>
 gj_status l2_tables_run(const Ctx& ctx, const K* rk2, int64_t nr, const L2Tables* t) {
-  constexpr int kW = L2Slot<K>::kWords;
   gj_status st;
   cudaStream_t s = ctx.stream;
-  if ((st = cuda_check(cudaMemsetAsync(t->bcounter, 0, sizeof(int), s))) != GJ_OK) return st;
+  // the chunk counter, then per partition its clearing-segment and cleared-segment counters
+  if ((st = cuda_check(cudaMemsetAsync(t->bcounter, 0, sizeof(int) * (1 + 2 * kL2Parts), s))) != GJ_OK) return st;
   if ((st = partition_bounds_run(ctx, sizeof(K) == 8 ? GJ_I64 : GJ_I32, rk2, nr, 0, kL2Bits, kHashed, t->roff)) !=
       GJ_OK)
     return st;
@@ -1401,13 +1441,12 @@ gj_status l2_tables_run(const Ctx& ctx, const K* rk2, int64_t nr, const L2Tables
     l2_table_offsets_kernel<<<1, kL2Parts, 0, s>>>(t->roff, t->toff);
   }
   LaunchScope ls(ctx, KK_NPHJ_BUILD);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((4 * nr + 1023) / 1024, (int64_t)ctx.num_sms * 8));
-  l2_table_clear_kernel<<<blocks, 256, 0, s>>>(t->table, t->toff, kW);
-  // blocks take build chunks in order: the tables being filled are those of a few
-  // neighbouring partitions
+  // blocks take build chunks in order: the tables being cleared and filled are
+  // those of a few neighbouring partitions
   const int bblocks =
       (int)std::max<int64_t>(1, std::min<int64_t>((nr + kL2BuildChunk - 1) / kL2BuildChunk, (int64_t)ctx.num_sms * 8));
-  l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk2, nr, t->toff, t->table, t->bcounter, ctx.d_status);
+  l2_build_kernel<K><<<bblocks, 256, 0, s>>>(rk2, nr, t->toff, t->table, t->bcounter, t->bcounter + 1,
+                                             t->bcounter + 1 + kL2Parts, ctx.d_status);
   return cuda_check(cudaGetLastError());
 }
 
