@@ -273,7 +273,7 @@ def bench_selector(gj, n_sample: int = 64):
             **{k: v for k, v in ev.items() if k != "n"}, "seconds": time.perf_counter() - t0}
 
 
-def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 6784.5):
+def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 6796.5):
     """One query: |R| = 2^20 ⋈ |S| = 2^22, GROUP BY R.pay mod 1024, SUM/COUNT(S.pay), not materialised."""
     import torch
     w = wl.join_groupby_workload()
@@ -297,7 +297,7 @@ def bench_one_query(gj, wl, steps: int = 20, cpu: bool = True, peak: float = 678
     return out
 
 
-def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6784.5):
+def bench_many_to_many(gj, wl, steps: int = 5, peak: float = 6796.5):
     """Many-to-many join (Sec. 5.1.9): |R| = |S| = 2^26, keys uniform from 2^25 keys,
     two int32 payloads per side; every (r, s) pair materialised (about 2^27 rows)."""
     import torch
@@ -337,7 +337,7 @@ def _seq_variants(gj, ws):
     return out
 
 
-def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6784.5):
+def bench_batch(gj, wl, steps: int = 5, cpu: bool = True, peak: float = 6796.5):
     """512 join + group-by instances: the batched plan with each query's variant chosen
     by the trained network (the cost model if the package ships none) vs 512 sequential
     gj_join_groupby calls whose AUTO follows the paper's rules."""

@@ -436,13 +436,13 @@ __device__ __forceinline__ bool emit_range(const K* __restrict__ skey, int64_t u
 // -1). Every warp owns a contiguous range of the unit and writes it without
 // block barriers, all loads of a group of columns in flight before its stores.
 // Called by all threads of the block after s_midx is complete.
-template <typename K>
+template <typename K, int NT = kThreads>
 __device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_t u0, int un, int64_t unit,
                                               int64_t nunits, const int32_t* s_midx, const JoinIO& io,
                                               uint64_t* unit_status, int* err, uint32_t* s_wcnt, uint64_t* s_base_p) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint64_t& s_base = *s_base_p;
-  constexpr int kWarpRows = kUnitRows / (kThreads / 32);
+  constexpr int kWarpRows = kUnitRows / (NT / 32);
   const int w0 = warp * kWarpRows, wend = min(w0 + kWarpRows, un);
   uint32_t cnt = 0;
   for (int i = w0 + lane; i < wend; i += 32) cnt += s_midx[i] >= 0 ? 1u : 0u;
@@ -451,7 +451,7 @@ __device__ __forceinline__ void phj_emit_unit(const K* __restrict__ skey, int64_
   if (lane == 0) s_wcnt[warp] = cnt;
   __syncthreads();
   if (warp == 0) {
-    uint32_t tot = lane < kThreads / 32 ? s_wcnt[lane] : 0u;
+    uint32_t tot = lane < NT / 32 ? s_wcnt[lane] : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     const uint64_t excl = lookback_scan_warp(unit_status, unit, tot, err);
@@ -810,8 +810,9 @@ __device__ __forceinline__ int32_t l2_resolve(const K* __restrict__ rkey, const 
   return -1;
 }
 
-template <typename K>
-__global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __restrict__ rkey,
+constexpr int kL2ProbeThreads = 256;
+template <typename K, int NT = kL2ProbeThreads>
+__global__ void __launch_bounds__(NT, 1024 / NT) phj_l2_probe_kernel(const K* __restrict__ rkey,
                                                                 const int64_t* __restrict__ toff,
                                                                 const int32_t* __restrict__ table,
                                                                 const K* __restrict__ skey, int64_t ns, JoinIO io,
@@ -820,11 +821,11 @@ __global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __re
   __shared__ int32_t s_midx[kUnitRows];
   __shared__ int64_t s_toff[kL2Parts + 1];
   __shared__ int64_t s_unit;
-  __shared__ uint32_t s_wcnt[kThreads / 32];
+  __shared__ uint32_t s_wcnt[NT / 32];
   __shared__ uint64_t s_base;
   const int t = threadIdx.x;
   if (t == 0) s_unit = atomicAdd(unit_counter, 1);
-  for (int p = t; p <= kL2Parts; p += kThreads) s_toff[p] = toff[p];
+  for (int p = t; p <= kL2Parts; p += NT) s_toff[p] = toff[p];
   __syncthreads();
   const int64_t unit = s_unit;
   if (unit >= nunits) return;
@@ -832,11 +833,11 @@ __global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __re
   const int un = (int)min64(kUnitRows, ns - u0);
   // every row's build row: kLook rows per thread in flight
   constexpr int kLook = 4;
-  for (int r0 = 0; r0 < un; r0 += kThreads * kLook) {
+  for (int r0 = 0; r0 < un; r0 += NT * kLook) {
     K k[kLook];
 #pragma unroll
     for (int q = 0; q < kLook; ++q) {
-      const int r = r0 + q * kThreads + t;
+      const int r = r0 + q * NT + t;
       k[q] = r < un ? __ldcs(skey + u0 + r) : K(0);
     }
     // the first slot of every row of the batch is read before any is resolved, so
@@ -851,19 +852,19 @@ __global__ void __launch_bounds__(kThreads, 4) phj_l2_probe_kernel(const K* __re
       base[q] = s_toff[P];  // in entries
       msk[q] = (uint64_t)(s_toff[P + 1] - s_toff[P]) - 1;
       sl[q] = (h >> kL2Bits) & msk[q];
-      const bool in = r0 + q * kThreads + t < un;
+      const bool in = r0 + q * NT + t < un;
       w[q] = in ? __ldg(reinterpret_cast<const typename L2Slot<K>::W*>(table) + base[q] + sl[q])
                 : typename L2Slot<K>::W(0);
     }
 #pragma unroll
     for (int q = 0; q < kLook; ++q) {
-      const int r = r0 + q * kThreads + t;
+      const int r = r0 + q * NT + t;
       if (r >= un) continue;
       s_midx[r] = l2_resolve<K>(rkey, table, base[q], msk[q], sl[q], w[q], k[q]);
     }
   }
   __syncthreads();
-  phj_emit_unit<K>(skey, u0, un, unit, nunits, s_midx, io, unit_status, err, s_wcnt, &s_base);
+  phj_emit_unit<K, NT>(skey, u0, un, unit, nunits, s_midx, io, unit_status, err, s_wcnt, &s_base);
 }
 
 // ---------------------------------------------------------------- NPHJ
@@ -1689,8 +1690,8 @@ gj_status join_typed(const Ctx& ctx, const gj_table* R, const gj_table* S, int v
   if ((st = cuda_check(cudaMemsetAsync(ucounter, 0, sizeof(int), s))) != GJ_OK) return st;
   if (l2) {
     LaunchScope ls(ctx, KK_PHJ_PROBE);
-    phj_l2_probe_kernel<K><<<(unsigned)nunits, kThreads, 0, s>>>(rk, l2t.toff, l2t.table, sk, ns, io, ustat, ucounter,
-                                                                  nunits, ctx.d_status);
+    phj_l2_probe_kernel<K><<<(unsigned)nunits, kL2ProbeThreads, 0, s>>>(rk, l2t.toff, l2t.table, sk, ns, io, ustat,
+                                                                         ucounter, nunits, ctx.d_status);
     return cuda_check(cudaGetLastError());
   }
   const size_t dyn = phj_unit_smem_bytes<K>();
