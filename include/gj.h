@@ -97,7 +97,11 @@ typedef enum {
                     count gives GJ_ERR_CAPACITY), else 2 x n */
   GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3), on the key
                     bits that vary only; synchronises the stream once to read the key range */
-  GJ_GB_PGB = 3, /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3) */
+  GJ_GB_PGB = 3, /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3); a partition
+                    with far more rows than the others (few groups, skew) is cut into slices aggregated by
+                    several blocks into partial rows, then merged (Sec. 4.3's remedy for overly large
+                    partitions); scratch for partial rows of up to the sliced partitions' rows, sized by
+                    one stream synchronisation when n x (key bytes + 8 x aggregates) exceeds 256 MB */
   GJ_GB_SGB_UR = 4, /* SGB with (key, tuple id) sorted and values gathered through the ids (GFUR, Sec. 4.1.2) */
   GJ_GB_PGB_UR = 5, /* PGB with (key, tuple id) partitioned and values gathered through the ids (GFUR) */
   GJ_GB_SGB_DE = 6  /* SGB on dictionary codes: dense group ids (HGB stage 1) sorted on ceil(log2 g) bits
@@ -373,8 +377,9 @@ gj_status gj_auto_variants(const gj_table* R, const gj_table* S, int32_t nagg, c
  * bytes (M1; B_R measured with the clustered-vs-unclustered gather of Table
  * gather-profile, gj_gather), or B_G / B_L2 times when the structure they go to
  * fits in l2_bytes; every kernel launch and host synchronisation adds a fixed
- * cost; the partition-based group-by pays for its hottest partition (share
- * 1 / H(g, z) of the rows under Zipf factor z) on one SM. Fields <= 0 that
+ * cost; the partition-based group-by pays for the contention on its hottest
+ * partition (share 1 / H(g, z) of the rows under Zipf factor z), counted as if
+ * one SM took those rows. Fields <= 0 that
  * name device figures (l2_bytes, smem_bytes, num_sms) are read from the current
  * device, or take GB300's when there is none. */
 typedef struct {
@@ -384,7 +389,7 @@ typedef struct {
   double smem_bytes;    /* shared memory per block for HGB's aggregates; 0 = the device's opt-in maximum */
   double launch_bytes;  /* fixed cost of one kernel launch, in bytes at B_G */
   double sync_bytes;    /* fixed cost of one host synchronisation inside a call */
-  double hot_row_bytes; /* bytes of work per row of the hottest PGB partition */
+  double hot_row_bytes; /* bytes of work per row of the hottest PGB partition (as if on one SM) */
   int32_t num_sms;      /* 0 = the device's */
   int32_t reserved;
 } gj_cost_params;
@@ -393,7 +398,7 @@ typedef struct {
  * than clustered ones over 2^27 int32, and the paper's reading of that gap,
  * B_G / B_R = 3 x gap - 2), B_G / B_L2 = 27.5 / 4.5 (the paper's B_L2 = 4.5 B_G),
  * launch 2e7 and synchronisation 6e7 bytes (about 3 and 9 us at 6.8 TB/s),
- * 20 bytes per hot-partition row. */
+ * 10 bytes per hot-partition row. */
 void gj_cost_params_default(gj_cost_params* p);
 /* Installs the parameters used by GJ_SELECT_COST (and by GJ_SELECT_MLP without
  * a network) in this process; NULL restores the defaults. Ratios below 1 or

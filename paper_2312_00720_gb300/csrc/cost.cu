@@ -13,9 +13,10 @@
 //     their bytes (the form of M4's B_M / min(g, 24) for an L2-resident table);
 //   * each kernel launch and each host synchronisation inside a call adds a fixed
 //     cost, which dominates small inputs;
-//   * the partition-based group-by aggregates one partition per thread block, so
-//     the partition holding the most frequent key (share 1 / H(g, z) of the rows
-//     under a Zipf factor z) is processed by one SM alone.
+//   * the partition-based group-by pays for its hottest partition (share 1 / H(g, z)
+//     of the rows under a Zipf factor z): sliced over several blocks, it still
+//     costs its rows' contention on the hot keys, counted as if one SM took them
+//     at hot_row_bytes each.
 // Host code only; it reads sizes, types and hints, never the data.
 #include <algorithm>
 #include <cmath>
@@ -136,11 +137,12 @@ void groupby_costs(const Model& m, const gj_table* in, int nagg, const int32_t* 
   c[3] = (k + 2 * ps * (k + 4)) * n + (k + 4) * n + m.rnd(w * n, w * n) + out + 10 * L + Y;
   c[5] = 2 * k * n + m.rnd((k + 4) * g, dict) + m.rnd((k + 4) * n, dict) + (4 + 2 * ps * (4 + w)) * n + (4 + w) * n +
          out + 12 * L;
-  // PGB: one pass up to 2^20 groups, else two; the hottest partition on one SM
+  // PGB: one pass up to 2^20 groups, else two; the hottest partition's contention
   const double pb = g <= (double)(1 << 20) ? 1 : 2;
   const double hot = zipf_top_share(g, z) * n * m.sms * m.p.hot_row_bytes;
-  c[2] = (k + 2 * pb * (k + w)) * n + (k + w) * n + out + 5 * L + hot;
-  c[4] = (k + 2 * pb * (k + 4)) * n + (k + 4) * n + m.rnd(w * n, w * n) + out + 6 * L + hot;
+  const double pgb_sync = n * (k + 8.0 * nagg) > 256.0 * 1048576.0 ? Y : 0.0;  // sizing its partial rows
+  c[2] = (k + 2 * pb * (k + w)) * n + (k + w) * n + out + 5 * L + hot + pgb_sync;
+  c[4] = (k + 2 * pb * (k + 4)) * n + (k + 4) * n + m.rnd(w * n, w * n) + out + 6 * L + hot + pgb_sync;
 }
 
 Model make_model() {
@@ -187,7 +189,7 @@ void gj_cost_params_default(gj_cost_params* p) {
   p->smem_bytes = 0;            // the device's opt-in shared memory per block (at most 200 KB)
   p->launch_bytes = 2.0e7;      // about 3 us at 6.8 TB/s
   p->sync_bytes = 6.0e7;        // a host round trip inside the call
-  p->hot_row_bytes = 20.0;
+  p->hot_row_bytes = 10.0;  // PGB slices its hottest partitions; what remains is contention on the hot keys
   p->num_sms = 0;
 }
 

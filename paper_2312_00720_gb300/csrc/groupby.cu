@@ -1167,6 +1167,90 @@ constexpr int kPgbMaxQ = 12;
 constexpr int kPgbSmem = 110 * 1024;  // dynamic shared memory budget of a block (two blocks per SM)
 constexpr int kPgbMaxCap = 4096;      // groups per round (local ids fit int16)
 
+// Work of a PGB launch beyond one block per partition. Partitions with many more
+// rows than the others (identical keys: few groups, Zipf skew) are cut into slices
+// taken by several blocks (items); a slice's groups go to partial rows in the
+// partition's own range of part_keys / part_agg (a partition's partial rows never
+// outnumber its rows), counted by pcount; a second launch with pcount set (and
+// no items) then aggregates each sliced partition's partial rows into the result
+// (Sec. 4.3: overly large partitions get a group-by of their own).
+struct PgbItem {
+  int32_t part;
+  int32_t nslices;
+  int64_t r0, r1;
+};
+template <typename K>
+struct PgbWork {
+  const PgbItem* items;        // non-null: block b takes items[b]
+  const int64_t* nitems;       // non-null: blocks from *nitems on have no item
+  unsigned long long* pcount;  // partial rows per partition (the second launch reads them)
+  const int64_t* pbase;        // first partial row of each sliced partition
+  K* part_keys;                // partial rows: keys and one int64 value per aggregate
+  int64_t* part_agg[kMaxAggs];
+};
+
+// Items of the first PGB launch (one block): every non-empty partition whole, or,
+// when it has more than `thresh` rows, in slices of about `slice` rows. info[0] =
+// the item count, info[1] = the rows of the sliced partitions; pbase[p] = where
+// partition p's partial rows start (sliced partitions packed in order).
+__global__ void __launch_bounds__(1024) pgb_items_kernel(const int64_t* __restrict__ poff, int nparts, int64_t thresh,
+                                                         int64_t slice, PgbItem* __restrict__ items,
+                                                         int64_t* __restrict__ pbase, int64_t* info) {
+  __shared__ int64_t s_w[2][32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int per = (nparts + 1023) / 1024;
+  const int p0 = min(t * per, nparts), p1 = min(p0 + per, nparts);
+  auto nslices = [&](int p) -> int64_t {
+    const int64_t rows = poff[p + 1] - poff[p];
+    if (rows <= 0) return 0;
+    return rows > thresh ? (rows + slice - 1) / slice : 1;
+  };
+  int64_t cnt = 0, srows = 0;
+  for (int p = p0; p < p1; ++p) {
+    const int64_t k = nslices(p);
+    cnt += k;
+    if (k > 1) srows += poff[p + 1] - poff[p];
+  }
+  // block-wide exclusive scans of both
+  int64_t x = cnt, y = srows;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t a = __shfl_up_sync(0xffffffffu, x, o), b = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= o) {
+      x += a;
+      y += b;
+    }
+  }
+  if (lane == 31) {
+    s_w[0][warp] = x;
+    s_w[1][warp] = y;
+  }
+  __syncthreads();
+  if (t == 0) {
+    int64_t a = 0, b = 0;
+    for (int w = 0; w < 32; ++w) {
+      const int64_t ca = s_w[0][w], cb = s_w[1][w];
+      s_w[0][w] = a;
+      s_w[1][w] = b;
+      a += ca;
+      b += cb;
+    }
+    info[0] = a;
+    info[1] = b;
+  }
+  __syncthreads();
+  int64_t ib = s_w[0][warp] + x - cnt, rb = s_w[1][warp] + y - srows;
+  for (int p = p0; p < p1; ++p) {
+    const int64_t k = nslices(p), r0 = poff[p], r1 = poff[p + 1];
+    pbase[p] = rb;
+    if (k > 1) rb += r1 - r0;
+    const int64_t len = k > 1 ? (r1 - r0 + k - 1) / k : r1 - r0;
+    for (int64_t q = 0; q < k; ++q)
+      items[ib + q] = PgbItem{p, (int32_t)k, r0 + q * len, min64(r1, r0 + (q + 1) * len)};
+    ib += k;
+  }
+}
+
 template <typename K>
 __device__ __forceinline__ uint32_t pgb_sub(K k, int q) {
   if (q == 0) return 0;
@@ -1195,7 +1279,7 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
                                                           const int64_t* __restrict__ poff, int pbits, Aggs A,
                                                           ColCache cc, SmemAggLayout L, int C,
                                                           K* __restrict__ out_keys, int64_t cap,
-                                                          unsigned long long* ngroups, int* err) {
+                                                          unsigned long long* ngroups, PgbWork<K> W, int* err) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   int32_t* s_slot = (int32_t*)s_raw;
   int16_t* s_lid = (int16_t*)(s_slot + 2 * C);
@@ -1211,10 +1295,31 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
   __shared__ int s_top;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t p = blockIdx.x;
-  const int64_t r0 = poff[p], r1 = poff[p + 1];
+  // the block's rows: a whole partition, one slice of a large one (whose groups go
+  // to the partial rows of the partition), or the partial rows of a sliced one
+  int64_t p = blockIdx.x, r0, r1;
+  bool partial = false;
+  if (W.items) {
+    if (W.nitems && (int64_t)blockIdx.x >= *W.nitems) return;
+    const PgbItem it = W.items[blockIdx.x];
+    p = it.part;
+    r0 = it.r0;
+    r1 = it.r1;
+    partial = it.nslices > 1;
+  } else if (W.pcount) {
+    r0 = W.pbase[p];
+    r1 = r0 + (int64_t)W.pcount[p];
+  } else {
+    r0 = poff[p];
+    r1 = poff[p + 1];
+  }
   if (r1 <= r0) return;
   const int64_t rows = r1 - r0;
+  K* __restrict__ okeys = partial ? W.part_keys : out_keys;
+  // the destination column of each aggregate, read from shared memory in the loops
+  __shared__ int64_t* oagg[kMaxAggs];
+  if (tid < A.n) oagg[tid] = partial ? W.part_agg[tid] : A.out[tid];
+  const int64_t ocap = partial ? INT64_MAX : cap;  // a partition's partial rows never exceed its rows
   int tslots = 64;  // table slots: about twice the rows, at most 2C
   while (tslots < 2 * C && tslots < 2 * rows) tslots <<= 1;
   if (tid == 0) {
@@ -1325,7 +1430,10 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
         offs[j] = o;
         o += (int64_t)cc_cap * L.width[j];
       }
-      s_base = atomicAdd(ngroups, (unsigned long long)count);  // the round's output rows
+      // the round's output rows: from the global group counter, or the partition's
+      // next partial rows
+      s_base = partial ? (unsigned long long)W.pbase[p] + atomicAdd(&W.pcount[p], (unsigned long long)count)
+                       : atomicAdd(ngroups, (unsigned long long)count);
     }
     if (tid < A.n) s_code[tid] = slot_code(A.op[tid], A.op[tid] == GJ_AGG_COUNT ? -1 : cc.slot[tid],
                                            slot_form(A, cc, tid, true));
@@ -1338,7 +1446,7 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
     // split SUMs accumulate in the output rows, folded in every kSplitRows rows
     for (int j = 0; j < A.n; ++j)
       if ((s_code[j] & 3) == kSlotSplit)
-        for (int l = tid; l < count && base + l < cap; l += blockDim.x) A.out[j][base + l] = 0;
+        for (int l = tid; l < count && base + l < ocap; l += blockDim.x) oagg[j][base + l] = 0;
     __syncthreads();
     auto fold_split = [&]() {
       for (int j = 0; j < A.n; ++j) {
@@ -1350,7 +1458,7 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
             v += slot_read(GJ_AGG_SUM, kSlotSplit, pp);
             *(int64_t*)pp = 0;
           }
-          if (base + l < cap) A.out[j][base + l] += v;  // this block owns the row
+          if (base + l < ocap) oagg[j][base + l] += v;  // this block owns the row
         }
       }
     };
@@ -1401,11 +1509,11 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
     // ---- the round's groups: keys and the other aggregates, copies combined
     for (int l = tid; l < count; l += blockDim.x) {
       const int64_t o = base + l;
-      if (o >= cap) {
+      if (o >= ocap) {
         over_cap = true;
         continue;
       }
-      out_keys[o] = s_key[l];
+      okeys[o] = s_key[l];
       for (int j = 0; j < A.n; ++j) {
         const int form = s_code[j] & 3;
         if (form == kSlotSplit) continue;
@@ -1413,7 +1521,7 @@ __global__ void __launch_bounds__(kPgbThreads, 2) pgb_kernel(const K* __restrict
         int64_t v = slot_read(A.op[j], form, sl);
         // copies a group never reached hold the identity, which combining leaves out
         for (int c = 1; c < ncopy; ++c) v = agg_combine(A.op[j], v, slot_read(A.op[j], form, sl + c * copy_bytes));
-        A.out[j][o] = v;
+        oagg[j][o] = v;
       }
     }
     __syncthreads();
@@ -1766,9 +1874,87 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     return st;
   const size_t dyn = (size_t)pgb_agg_off<K>(C) + (size_t)C * L.bytes_per_group;
   if ((st = ensure_smem_attr(ctx, (const void*)pgb_kernel<K>, (int)dyn)) != GJ_OK) return st;
-  LaunchScope ls(ctx, KK_PGB);
-  pgb_kernel<K><<<(unsigned)nparts, kPgbThreads, dyn, s>>>(k2, poff, bits, A, make_col_cache(A), L, C, (K*)out_keys,
-                                                           cap, (unsigned long long*)d_ngroups, ctx.d_status);
+  // partitions of more than four slices' rows (few groups, hot keys) are cut into
+  // slices of about `slice` rows: an SM's fair share of the rows (a sixteenth of
+  // that when the average partition is smaller), at least 16384
+  const int64_t avg = std::max<int64_t>(1, n / nparts);
+  const int64_t slice = std::max<int64_t>(16384, std::min<int64_t>(avg, n / ((int64_t)ctx.num_sms * 8)));
+  const int64_t thresh = 4 * slice;
+  PgbItem* items = scr.get_as<PgbItem>((size_t)(nparts + n / slice + 2));
+  int64_t* pbase = scr.get_as<int64_t>(nparts);
+  int64_t* info = scr.get_as<int64_t>(2);
+  unsigned long long* pcount = scr.get_as<unsigned long long>(nparts);
+  if (scr.failed()) return GJ_ERR_OOM;
+  if ((st = cuda_check(cudaMemsetAsync(pcount, 0, sizeof(unsigned long long) * nparts, s))) != GJ_OK) return st;
+  {
+    LaunchScope ls(ctx, KK_PGB);
+    pgb_items_kernel<<<1, 1024, 0, s>>>(poff, (int)nparts, thresh, slice, items, pbase, info);
+  }
+  PgbWork<K> W{};
+  W.items = items;
+  W.pcount = pcount;
+  W.pbase = pbase;
+  // partial rows never outnumber the sliced partitions' rows. Small inputs take
+  // scratch for all n rows and launch for the largest item count (blocks past it
+  // leave at once); large ones read the item count and the sliced rows first
+  // (one synchronisation) to size both exactly
+  const size_t part_row_bytes = sizeof(K) + (size_t)8 * nagg;
+  const bool sized_up_front = (size_t)n * part_row_bytes <= ((size_t)256 << 20);
+  int64_t nitems = nparts + n / slice + 2, sliced_rows = n;
+  if (sized_up_front) {
+    W.nitems = info;
+  } else {
+    int64_t h_info[2] = {0, 0};
+    if ((st = cuda_check(cudaMemcpyAsync(h_info, info, sizeof(h_info), cudaMemcpyDeviceToHost, s))) != GJ_OK)
+      return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s))) != GJ_OK) return st;
+    nitems = h_info[0];
+    sliced_rows = h_info[1];
+    if (nitems == 0) return GJ_OK;
+  }
+  if (sliced_rows > 0) {
+    W.part_keys = scr.get_as<K>((size_t)sliced_rows);
+    for (int j = 0; j < nagg; ++j) W.part_agg[j] = scr.get_as<int64_t>((size_t)sliced_rows);
+    if (scr.failed()) return GJ_ERR_OOM;
+  }
+  {
+    LaunchScope ls(ctx, KK_PGB);
+    pgb_kernel<K><<<(unsigned)nitems, kPgbThreads, dyn, s>>>(k2, poff, bits, A, make_col_cache(A), L, C,
+                                                             (K*)out_keys, cap, (unsigned long long*)d_ngroups, W,
+                                                             ctx.d_status);
+  }
+  if (sliced_rows == 0) return cuda_check(cudaGetLastError());
+  // the sliced partitions' partial rows, one block each: COUNTs add up, SUM / MIN /
+  // MAX combine as themselves, over int64 values
+  Aggs A2 = A;
+  A2.tid = nullptr;
+  for (int j = 0; j < nagg; ++j) {
+    A2.op[j] = ops[j] == GJ_AGG_COUNT ? GJ_AGG_SUM : ops[j];
+    A2.src[j] = W.part_agg[j];
+    A2.size[j] = 8;
+  }
+  SmemAggLayout L2{};
+  {
+    int q = 0;
+    for (int j = 0; j < nagg; ++j) {
+      L2.width[j] = 8;
+      L2.order[q++] = j;
+      L2.bytes_per_group += 8;
+    }
+  }
+  int C2 = kPgbMaxCap;
+  while (C2 > 32 && pgb_agg_off<K>(C2) + C2 * L2.bytes_per_group > kPgbSmem) C2 >>= 1;
+  const size_t dyn2 = (size_t)pgb_agg_off<K>(C2) + (size_t)C2 * L2.bytes_per_group;
+  if ((st = ensure_smem_attr(ctx, (const void*)pgb_kernel<K>, (int)std::max(dyn, dyn2))) != GJ_OK) return st;
+  PgbWork<K> W2 = W;
+  W2.items = nullptr;
+  W2.nitems = nullptr;
+  {
+    LaunchScope ls(ctx, KK_PGB);
+    pgb_kernel<K><<<(unsigned)nparts, kPgbThreads, dyn2, s>>>(W.part_keys, poff, bits, A2, make_col_cache(A2), L2, C2,
+                                                              (K*)out_keys, cap, (unsigned long long*)d_ngroups, W2,
+                                                              ctx.d_status);
+  }
   return cuda_check(cudaGetLastError());
 }
 

@@ -180,3 +180,36 @@ def test_hgb_few_groups_pass_extreme_values_and_wide_columns(gj):
     wide = rng.integers(-(2**62), 2**62, n, dtype=np.int64)
     got = oracle.canonical(run_gb(gj, key, [wide], aggs, cols, "hgb", groups_hint=20))
     assert np.array_equal(got, want_rows(key, [wide], aggs, cols))
+
+
+def _hot_mix(n, hot_frac, n_other, seed):
+    """Keys: a hot_frac share of the rows on one key, the rest uniform over n_other keys."""
+    rng = np.random.default_rng(seed)
+    key = rng.integers(-(2**31), 2**31, n_other, dtype=np.int64).astype(np.int32)[rng.integers(0, n_other, n)]
+    key[rng.random(n) < hot_frac] = 123456789
+    vals = [rng.integers(-(2**20), 2**20, n).astype(np.int32) for _ in range(3)]
+    return key, vals
+
+
+@pytest.mark.parametrize("variant", ["pgb", "pgb_ur"])
+@pytest.mark.parametrize("case", ["few_groups", "zipf", "hot_key_many_groups", "hot_key_wrong_hint"])
+def test_pgb_slices_large_partitions(gj, variant, case):
+    """Partitions far larger than the average are cut into slices aggregated by
+    several blocks into partial rows, then merged: few groups (every non-empty
+    partition sliced), Zipf skew, and a hot key whose partition also holds more
+    distinct keys than one block can (sub-rounds in the slices and in the merge)."""
+    n = 1 << 22
+    if case == "few_groups":
+        w = wl.groupby_workload(n, 16, nvals=3, seed=5)
+        key, vals, hint = w["key"], w["vals"], 16
+    elif case == "zipf":
+        w = wl.groupby_workload(n, 1 << 12, nvals=3, theta=1.2, seed=6)
+        key, vals, hint = w["key"], w["vals"], 1 << 12
+    elif case == "hot_key_many_groups":
+        key, vals = _hot_mix(n, 0.5, 1 << 20, seed=7)
+        hint = 1 << 10  # too small: partitions hold several rounds' worth of keys
+    else:
+        key, vals = _hot_mix(n, 0.3, 1 << 16, seed=8)
+        hint = 0
+    got = oracle.canonical(run_gb(gj, key, vals, AGGS, COLS, variant, groups_hint=hint))
+    assert np.array_equal(got, want_rows(key, vals, AGGS, COLS))
