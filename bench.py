@@ -494,7 +494,8 @@ def kernel_families():
     Joins |R| = 2^22, |S| = 2^24 with 4 + 4 int32 payloads (PHJ-TR, PHJ-UR, NPHJ,
     SMJ-TR); NPHJ-MN on 2^22 x 2^22 rows over 2^21 keys; the one-query fused
     join -> group-by (NPHJ and PHJ-TR plans); group-by of 2^24 rows with 10
-    aggregates (HGB over 2^4 and 2^12 ids, PGB and SGB over 2^20); a 64-instance batch;
+    aggregates (HGB over 2^4 and 2^12 ids, PGB over 2^4 (sliced partitions) and 2^20,
+    SGB over 2^20); a 64-instance batch;
     one selector training step (loss + gradient, Adam)."""
     import numpy as np
     import torch
@@ -519,7 +520,7 @@ def kernel_families():
         gj.join_groupby(*qargs, variant=v)
     aggs = ["count"] + ["sum", "min", "max"] * 3
     cols = [0, 0, 0, 0, 1, 1, 1, 2, 2, 2]
-    for lg, v in ((4, "hgb"), (12, "hgb"), (20, "pgb"), (20, "sgb")):
+    for lg, v in ((4, "hgb"), (4, "pgb"), (12, "hgb"), (20, "pgb"), (20, "sgb")):
         g = wl.groupby_workload(1 << 24, 1 << lg, nvals=3, seed=7)
         gj.groupby(d(g["key"]), [d(x) for x in g["vals"]], aggs, cols, variant=v, groups_hint=1 << lg)
     ws = wl.batch_workload(64, seed=7)
