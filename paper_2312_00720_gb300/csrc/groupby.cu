@@ -642,6 +642,322 @@ __global__ void __launch_bounds__(1024, 1) hgb_tiny_kernel(const K* __restrict__
   }
 }
 
+// ---------------------------------------------------------------- HGB, at most 16 groups
+// When the groups hint says at most kFewKeys groups, each block counting-sorts
+// every tile of kFewTile rows by local group id in shared memory and reduces the
+// runs. Keys get local ids 0..15 from the block's 64-slot table of tagged keys;
+// keys enter it only in insertion phases between block barriers, taken when some
+// thread meets a key the table lacks, so the lookups in between read a table that
+// nothing writes. Per tile:
+//  A. every row's id; four ballots on its bits give each row its rank among the
+//     warp's rows of its group, and one shared-memory atomic per group and warp
+//     reserves the warp's places in that group's run;
+//  B. the groups' sizes become run offsets (and are added to the groups' COUNTs);
+//  C. every row's cached values go to their places;
+//  D. one warp per group walks its run and folds it into registers: per lane the
+//     64-bit SUM, the MIN and the MAX of each column for that group.
+// No update of a result conflicts with another and no work crosses lanes except
+// the ballots and shuffles of the ranking. The tiles' key and value columns reach
+// shared memory by bulk copies kFewStages - 1 tiles ahead of their use (one thread
+// refills a stage once the block has read it); the ragged last tile, and inputs
+// whose columns do not start on 16 bytes, are read with plain loads. Two blocks
+// share an SM, so that one block's work overlaps the other's barriers. At the end
+// each warp reduces its lanes and the block leaves one TinyPart per id for the
+// merge kernel. A 17th key in a block, or a key equal to the empty tag, sets
+// `overflow`, and the general HGB kernels run instead.
+constexpr int kFewKeys = 16;
+constexpr int kFewThreads = 512;
+constexpr int kFewRows = 4;  // rows per thread per tile
+constexpr int kFewTile = kFewThreads * kFewRows;
+constexpr int kFewStages = 2;  // two blocks per SM must fit: 2 x (2 stages + the sorted tile)
+template <typename K, int NC>
+constexpr int few_stage_bytes() {
+  return kFewTile * (int)sizeof(K) + NC * kFewTile * 4;
+}
+static_assert(kFewKeys == 16 && kFewThreads == 32 * kFewKeys, "four ballots address the ids; one warp per group");
+
+// Local id of `tag` in the block's table, or -1 when it is absent.
+__device__ __forceinline__ int few_find(const unsigned long long* s_tab, const int* s_lid, unsigned long long tag,
+                                        unsigned long long empty) {
+  uint32_t sl = (uint32_t)((tag * 0x9e3779b97f4a7c15ull) >> 58);
+  for (int p = 0; p < kTinySlots; ++p) {
+    const unsigned long long w = s_tab[sl];
+    if (w == tag) return s_lid[sl];
+    if (w == empty) return -1;
+    sl = (sl + 1) & (kTinySlots - 1);
+  }
+  return -1;
+}
+
+// Keys and cached columns of this thread's rows of tile t (rows past n read nothing).
+template <typename K, int NV>
+__device__ __forceinline__ void few_load(const K* __restrict__ key, const ColCache& cc, int64_t n, int64_t t,
+                                         K (&kk)[kFewRows], int32_t (&v)[NV][kFewRows]) {
+  const int64_t base = t * kFewTile + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kFewRows; ++u) {
+    const int64_t i = base + (int64_t)u * kFewThreads;
+    const bool ok = i < n;
+    kk[u] = ok ? __ldcs(key + i) : K(0);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c][u] = (ok && c < cc.n) ? __ldcs(cc.src[c] + i) : 0;
+  }
+}
+
+template <typename K, int NC>
+__global__ void __launch_bounds__(kFewThreads, 2) hgb_few_kernel(const K* __restrict__ key, int64_t n, ColCache cc,
+                                                                 TinyPart* __restrict__ parts, int* overflow,
+                                                                 bool bulk, int* err) {
+  constexpr int NV = NC > 0 ? NC : 1;
+  constexpr unsigned F = 0xffffffffu;
+  constexpr int SB = few_stage_bytes<K, NC>();
+  extern __shared__ __align__(16) unsigned char few_stage[];  // kFewStages x (keys, columns), when bulk
+  __shared__ __align__(8) uint64_t s_bar[kFewStages];
+  __shared__ int32_t s_val[NV][kFewTile];  // the tile's values in group order
+  __shared__ unsigned long long s_tab[kTinySlots];
+  __shared__ int s_lid[kTinySlots];
+  __shared__ unsigned long long s_ltag[kFewKeys];
+  __shared__ int s_nkeys;
+  __shared__ int s_gcnt[kFewKeys];                  // the tile's rows per group (phase A)
+  __shared__ int s_gstart[kFewKeys + 1];            // the tile's run offsets (phase B)
+  __shared__ unsigned long long s_total[kFewKeys];  // COUNT per group over the block's tiles
+  __shared__ long long s_rsum[NV][kFewKeys];
+  __shared__ int s_rmn[NV][kFewKeys];
+  __shared__ int s_rmx[NV][kFewKeys];
+  const unsigned long long empty = seen_empty<K>();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kTinySlots) {
+    s_tab[tid] = empty;
+    s_lid[tid] = -1;
+  }
+  if (tid < kFewKeys) {
+    s_gcnt[tid] = 0;
+    s_total[tid] = 0ull;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      s_rsum[c][tid] = 0;
+      s_rmn[c][tid] = INT32_MAX;
+      s_rmx[c][tid] = INT32_MIN;
+    }
+  }
+  if (tid == 0) {
+    s_nkeys = 0;
+    if (bulk) {
+      for (int j = 0; j < kFewStages; ++j) mbar_init(&s_bar[j], 1);
+      mbar_fence_init();
+    }
+  }
+  __syncthreads();
+  const int64_t ntiles = (n + kFewTile - 1) / kFewTile;
+  const int64_t nk = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // this block's tiles
+  // the block's k-th tile comes by bulk copy unless it is the ragged last one
+  auto staged = [&](int64_t k) {
+    return bulk && !((n % kFewTile) != 0 && (int64_t)blockIdx.x + k * gridDim.x == ntiles - 1);
+  };
+  auto issue = [&](int64_t k) {  // one thread: tile k's columns into stage k mod kFewStages
+    const int64_t r = ((int64_t)blockIdx.x + k * gridDim.x) * kFewTile;
+    unsigned char* d = few_stage + (k % kFewStages) * SB;
+    uint64_t* bar = &s_bar[k % kFewStages];
+    mbar_expect_tx(bar, SB);
+    bulk_g2s(d, key + r, kFewTile * (int)sizeof(K), bar);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) bulk_g2s(d + kFewTile * sizeof(K) + c * kFewTile * 4, cc.src[c] + r, kFewTile * 4, bar);
+  };
+  if (tid == 0)
+    for (int64_t k = 0; k < kFewStages && k < nk; ++k)
+      if (staged(k)) issue(k);
+  // per id bit: all ones where this lane's group (lane & 15) has a 0, so that
+  // (ballot ^ mask) keeps the lanes whose row agrees with the group on that bit
+  const int G = lane & (kFewKeys - 1);
+  const unsigned xm0 = (G & 1) ? 0u : F, xm1 = (G & 2) ? 0u : F, xm2 = (G & 4) ? 0u : F, xm3 = (G & 8) ? 0u : F;
+  const unsigned below = (1u << lane) - 1u;
+  const int dg = warp;  // phase D: this warp's group
+  int64_t sum[NV];
+  int32_t mn[NV], mx[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    sum[c] = 0;
+    mn[c] = INT32_MAX;
+    mx[c] = INT32_MIN;
+  }
+  bool over = false;
+  int64_t k = 0;
+  // the bound is the same for all threads of the block: every barrier below is reached by all
+  for (; k < nk; ++k) {
+    const int64_t t = (int64_t)blockIdx.x + k * gridDim.x;
+    const int64_t base = t * kFewTile + tid;
+    K kk[kFewRows];
+    int32_t v[NV][kFewRows];
+    if (staged(k)) {
+      mbar_wait(&s_bar[k % kFewStages], (uint32_t)((k / kFewStages) & 1), err);
+      const unsigned char* d = few_stage + (k % kFewStages) * SB;
+#pragma unroll
+      for (int u = 0; u < kFewRows; ++u) {
+        kk[u] = reinterpret_cast<const K*>(d)[tid + u * kFewThreads];
+#pragma unroll
+        for (int c = 0; c < NV; ++c)
+          v[c][u] = c < NC ? reinterpret_cast<const int32_t*>(d + kFewTile * sizeof(K) + c * kFewTile * 4)[tid + u * kFewThreads] : 0;
+      }
+    } else {
+      few_load<K, NV>(key, cc, n, t, kk, v);
+    }
+    int lid[kFewRows];
+    bool miss = false;
+#pragma unroll
+    for (int u = 0; u < kFewRows; ++u) {
+      lid[u] = -2;  // past the end
+      if (base + (int64_t)u * kFewThreads < n) {
+        const unsigned long long tag = seen_tag<K>(kk[u]);
+        lid[u] = tag == empty ? -1 : few_find(s_tab, s_lid, tag, empty);
+        miss |= lid[u] == -1;
+      }
+    }
+    const bool any_miss = __syncthreads_or(miss);
+    // every thread has read stage k: it takes tile k + kFewStages
+    if (tid == 0 && k + kFewStages < nk && staged(k + kFewStages)) {
+      fence_proxy_async();
+      issue(k + kFewStages);
+    }
+    if (any_miss) {
+      // insertion phase: absent keys claim a slot; the claiming thread hands out the id
+      bool bail = false;
+#pragma unroll
+      for (int u = 0; u < kFewRows; ++u) {
+        if (lid[u] != -1) continue;
+        const unsigned long long tag = seen_tag<K>(kk[u]);
+        if (tag == empty) {
+          bail = true;
+          continue;
+        }
+        uint32_t sl = (uint32_t)((tag * 0x9e3779b97f4a7c15ull) >> 58);
+        bool placed = false;
+        for (int p = 0; p < kTinySlots && !placed; ++p) {
+          const unsigned long long w = atomicCAS(&s_tab[sl], empty, tag);
+          if (w == empty) {
+            const int l = atomicAdd(&s_nkeys, 1);
+            if (l < kFewKeys) {
+              s_lid[sl] = l;
+              s_ltag[l] = tag;
+            } else {
+              bail = true;
+            }
+            placed = true;
+          } else if (w == tag) {
+            placed = true;
+          } else {
+            sl = (sl + 1) & (kTinySlots - 1);
+          }
+        }
+        if (!placed) bail = true;
+      }
+      if (__syncthreads_or(bail)) {  // the same for all threads of the block
+        over = true;
+        break;
+      }
+      bool lost = false;
+#pragma unroll
+      for (int u = 0; u < kFewRows; ++u)
+        if (lid[u] == -1) {
+          lid[u] = few_find(s_tab, s_lid, seen_tag<K>(kk[u]), empty);
+          lost |= lid[u] < 0;
+        }
+      if (__syncthreads_or(lost)) {
+        over = true;
+        break;
+      }
+    }
+    // A: ranks within the warp's rows of each group, the warp's places reserved per group
+    int off[kFewRows];
+#pragma unroll
+    for (int u = 0; u < kFewRows; ++u) {
+      const bool valid = lid[u] >= 0;
+      const int l = valid ? lid[u] : 0;
+      const unsigned V = __ballot_sync(F, valid);
+      const unsigned b0 = __ballot_sync(F, l & 1), b1 = __ballot_sync(F, l & 2);
+      const unsigned b2 = __ballot_sync(F, l & 4), b3 = __ballot_sync(F, l & 8);
+      const unsigned m = V & (b0 ^ xm0) & (b1 ^ xm1) & (b2 ^ xm2) & (b3 ^ xm3);  // rows of group G
+      int wb = 0;
+      if (lane < kFewKeys && m) wb = atomicAdd(&s_gcnt[lane], __popc(m));
+      const unsigned pm = __shfl_sync(F, m, l);  // rows of this row's group
+      off[u] = __shfl_sync(F, wb, l) + __popc(pm & below);
+    }
+    __syncthreads();
+    // B: run offsets (exclusive sums of the groups' sizes from independent loads,
+    // no shuffle chain) and COUNTs; the sizes are cleared after the next barrier
+    if (warp == 0 && lane <= kFewKeys) {
+      int x = 0, c = 0;
+#pragma unroll
+      for (int j = 0; j < kFewKeys; ++j) {
+        const int y = s_gcnt[j];
+        x += j < lane ? y : 0;
+        c = j == lane ? y : c;
+      }
+      s_gstart[lane] = x;
+      if (lane < kFewKeys) s_total[lane] += (unsigned long long)c;
+    }
+    __syncthreads();
+    if (tid < kFewKeys) s_gcnt[tid] = 0;  // read only in B; next written after two more barriers
+    // C: values to their places
+#pragma unroll
+    for (int u = 0; u < kFewRows; ++u)
+      if (lid[u] >= 0) {
+        const int p = s_gstart[lid[u]] + off[u];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s_val[c][p] = v[c][u];
+      }
+    __syncthreads();
+    // D: this warp's half of its group's run
+    const int s1 = s_gstart[dg + 1];
+    for (int i = s_gstart[dg] + lane; i < s1; i += 32) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int32_t x = s_val[c][i];
+        sum[c] += x;
+        mn[c] = min(mn[c], x);
+        mx[c] = max(mx[c], x);
+      }
+    }
+  }
+  if (over) {
+    // the copies still in flight (tiles k + 1 .. k + kFewStages) land before the block leaves
+    if (tid == 0) {
+      atomicExch(overflow, 1);
+      for (int64_t j = k + 1; j <= k + kFewStages && j < nk; ++j)
+        if (staged(j)) mbar_wait(&s_bar[j % kFewStages], (uint32_t)((j / kFewStages) & 1), err);
+    }
+    return;
+  }
+  // each warp's lanes reduced into its group's results, one TinyPart per id
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    long long s = sum[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(F, s, o);
+    const int a = __reduce_min_sync(F, mn[c]), b = __reduce_max_sync(F, mx[c]);
+    if (lane == 0 && dg < s_nkeys) {
+      atomicAdd((unsigned long long*)&s_rsum[c][dg], (unsigned long long)s);
+      atomicMin(&s_rmn[c][dg], a);
+      atomicMax(&s_rmx[c][dg], b);
+    }
+  }
+  __syncthreads();
+  if (tid < kTinySlots) {
+    TinyPart tp{};
+    tp.tag = empty;
+    if (tid < s_nkeys) {
+      tp.tag = s_ltag[tid];
+      tp.count = (unsigned int)s_total[tid];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        tp.sum[c] = s_rsum[c][tid];
+        tp.mn[c] = s_rmn[c][tid];
+        tp.mx[c] = s_rmx[c][tid];
+      }
+    }
+    parts[(int64_t)blockIdx.x * kTinySlots + tid] = tp;
+  }
+}
+
 // Merges the blocks' slots (one block): dense group ids in order of first
 // appearance, the aggregates of Aggs from the per-column results, g into
 // *ngroups. Sets `overflow` instead when the union of keys is too large.
@@ -1636,7 +1952,8 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
   if ((st = cuda_check(cudaMemsetAsync(d_ngroups, 0, sizeof(int64_t), s))) != GJ_OK) return st;
   if (n == 0) return GJ_OK;
 
-  // HGB with at most 32 expected groups: the few-groups pass first; the general
+  // HGB with at most 32 expected groups: a few-groups pass first (tiles sorted by
+  // group in shared memory for at most 16, the lane-slot pass for 17 to 32); the general
   // kernels below run only if it reports overflow
   int* gate = nullptr;
   if (variant == GJ_GB_HGB && opt->groups_hint > 0 && opt->groups_hint <= kTinyKeys) {
@@ -1646,12 +1963,34 @@ gj_status groupby_typed(const Ctx& ctx, const gj_table* in, int nagg, const int3
     for (int j = 0; j < nagg; ++j)
       if (ops[j] != GJ_AGG_COUNT && (A0.size[j] != 4 || cc0.slot[j] < 0)) eligible = false;
     if (eligible) {
-      const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 2));
+      const bool few = opt->groups_hint <= kFewKeys;
+      const int64_t few_block_rows = kFewTile;
+      const int blocks =
+          few ? (int)std::max<int64_t>(1, std::min<int64_t>((n + few_block_rows - 1) / few_block_rows,
+                                                            (int64_t)ctx.num_sms * 2))
+              : (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)ctx.num_sms * 2));
       TinyPart* parts = scr.get_as<TinyPart>((size_t)blocks * kTinySlots);
       gate = scr.get_as<int>(1);
       if (scr.failed()) return GJ_ERR_OOM;
       if ((st = cuda_check(cudaMemsetAsync(gate, 0, sizeof(int), s))) != GJ_OK) return st;
-      {
+      if (few) {
+        static_assert(kColCache == 3, "one instantiation per cached-column count");
+        auto kern = cc0.n == 0   ? hgb_few_kernel<K, 0>
+                    : cc0.n == 1 ? hgb_few_kernel<K, 1>
+                    : cc0.n == 2 ? hgb_few_kernel<K, 2>
+                                 : hgb_few_kernel<K, 3>;
+        const int sb = cc0.n == 0   ? few_stage_bytes<K, 0>()
+                       : cc0.n == 1 ? few_stage_bytes<K, 1>()
+                       : cc0.n == 2 ? few_stage_bytes<K, 2>()
+                                    : few_stage_bytes<K, 3>();
+        // bulk copies need every column to start on 16 bytes (tiles then do too)
+        bool bulk = ((uintptr_t)in->key & 15) == 0;
+        for (int c = 0; c < cc0.n; ++c) bulk = bulk && ((uintptr_t)cc0.src[c] & 15) == 0;
+        const int bytes = bulk ? kFewStages * sb : 0;
+        if ((st = ensure_smem_attr(ctx, (const void*)kern, kFewStages * sb)) != GJ_OK) return st;
+        LaunchScope ls(ctx, KK_HGB_AGG);
+        kern<<<blocks, kFewThreads, bytes, s>>>((const K*)in->key, n, cc0, parts, gate, bulk, ctx.d_status);
+      } else {
         LaunchScope ls(ctx, KK_HGB_AGG);
         hgb_tiny_kernel<K><<<blocks, 1024, 0, s>>>((const K*)in->key, n, cc0, parts, gate);
       }

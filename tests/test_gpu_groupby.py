@@ -166,6 +166,64 @@ def test_hgb_few_groups_pass(gj, n, g, kdt, theta, hint):
     assert np.array_equal(got, want_rows(w["key"], w["vals"], AGGS, COLS))
 
 
+@pytest.mark.parametrize("case", ["count_only", "one_column", "two_columns_int64", "ragged_large",
+                                  "seventeen_keys", "int64_min_key", "sums_past_32_bits"])
+def test_hgb_sorted_tiles_pass(gj, case):
+    """Hints of at most 16 groups take the pass that sorts tiles by group in shared
+    memory: every cached-column count (0 to 3), ragged tails over many tiles, a
+    17th key or the reserved 8-byte key (the general path takes over, with bulk
+    copies still in flight), sums past 32 bits."""
+    rng = np.random.default_rng(len(case))
+    aggs, cols, hint = AGGS, COLS, 16
+    if case == "count_only":
+        n = (1 << 20) + 3
+        key = rng.integers(-8, 8, n).astype(np.int32)
+        vals, aggs, cols = [rng.integers(-5, 5, n).astype(np.int32)], ["count"], [0]
+    elif case == "one_column":
+        w = wl.groupby_workload((1 << 22) + 5, 12, nvals=1, theta=1.0, seed=3)
+        key, vals, hint = w["key"], w["vals"], 12
+        aggs, cols = ["max", "count", "sum", "min"], [0, 0, 0, 0]
+    elif case == "two_columns_int64":
+        w = wl.groupby_workload(999999, 16, nvals=2, key_dtype=np.int64, seed=4)
+        key, vals = w["key"], w["vals"]
+        aggs, cols = ["sum", "min", "max", "sum", "count"], [0, 0, 1, 1, 0]
+    elif case == "ragged_large":
+        w = wl.groupby_workload((1 << 24) + 777, 16, nvals=3, seed=5)
+        key, vals = w["key"], w["vals"]
+    elif case == "seventeen_keys":
+        w = wl.groupby_workload(1 << 20, 17, nvals=3, seed=6)
+        key, vals = w["key"], w["vals"]
+        assert len(np.unique(key)) == 17
+    elif case == "int64_min_key":
+        n = 300000
+        key = rng.integers(0, 4, n).astype(np.int64)
+        key[rng.random(n) < 0.25] = np.iinfo(np.int64).min
+        vals = [rng.integers(-1000, 1000, n).astype(np.int32) for _ in range(3)]
+        hint = 5
+    else:
+        n = 1 << 21
+        key = rng.integers(0, 3, n).astype(np.int32)
+        vals = [np.full(n, np.iinfo(np.int32).max, np.int32), np.full(n, np.iinfo(np.int32).min, np.int32),
+                rng.integers(2**30, 2**31, n).astype(np.int32)]
+    got = oracle.canonical(run_gb(gj, key, vals, aggs, cols, "hgb", groups_hint=hint))
+    assert np.array_equal(got, want_rows(key, vals, aggs, cols))
+
+
+@pytest.mark.parametrize("kdt", [np.int32, np.int64])
+def test_hgb_sorted_tiles_unaligned_columns(gj, kdt):
+    """Columns that do not start on 16 bytes are read with plain loads instead of
+    bulk copies: views one row into their buffers."""
+    w = wl.groupby_workload((1 << 21) + 1, 16, nvals=3, key_dtype=kdt, theta=0.5, seed=9)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    key, vals = dev(w["key"])[1:], [dev(v)[1:] for v in w["vals"]]
+    assert key.data_ptr() % 16 != 0
+    okeys, outs, ng = gj.groupby(key, vals, AGGS, COLS, variant="hgb", groups_hint=16)
+    g = int(ng.item())
+    got = np.stack([okeys[:g].cpu().numpy().astype(np.int64)] + [o[:g].cpu().numpy() for o in outs], 1)
+    want = want_rows(w["key"][1:], [v[1:] for v in w["vals"]], AGGS, COLS)
+    assert np.array_equal(oracle.canonical(got), want)
+
+
 def test_hgb_few_groups_pass_extreme_values_and_wide_columns(gj):
     rng = np.random.default_rng(23)
     n = 100000
