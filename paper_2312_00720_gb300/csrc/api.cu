@@ -133,7 +133,7 @@ gj_status make_ctx(void* stream, Ctx* ctx) {
   }
   if (!g_pool_configured[dev]) {
     // keep freed scratch in the stream-ordered pool instead of returning it to
-    // the driver after every call
+    // the CUDA driver after every call
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       uint64_t thr = UINT64_MAX;
