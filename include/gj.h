@@ -94,7 +94,11 @@ typedef enum {
   GJ_GB_AUTO = 0,
   GJ_GB_HGB = 1, /* hash-based, dense group ids then shared-memory aggregation (Sec. 4.2, Alg. 1); its
                     dictionary table holds 2 x groups_hint entries when a hint is set (a larger group
-                    count gives GJ_ERR_CAPACITY), else 2 x n */
+                    count gives GJ_ERR_CAPACITY), else 2 x n. With 1 <= groups_hint <= 32 and only COUNT
+                    and aggregates over 4-byte columns (at most three distinct), a single pass without
+                    dictionary runs first (up to 16: tiles sorted by group in shared memory; 17 to 32:
+                    lane-held aggregates); when the data holds more keys than that pass takes, it gives
+                    way to the dictionary path, with the same result */
   GJ_GB_SGB = 2, /* sort-based with the values sorted alongside the key (SGB-TR, Sec. 4.1.3), on the key
                     bits that vary only; synchronises the stream once to read the key range */
   GJ_GB_PGB = 3, /* partition-based with per-partition shared-memory tables (PGB-TR, Sec. 4.3); a partition
